@@ -1,0 +1,144 @@
+"""Pins of the oracle's quasi-random Fermi-Dirac sampling (paper §2.1, Appendix A)."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import neutrinos as nu
+
+ZETA3 = 1.2020569031595942
+ZETA5 = 1.0369277551433699
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_counts.json")
+
+
+@pytest.fixture(scope="module")
+def table10():
+    return nu.shell_table(10, [0.2 / 3] * 3)
+
+
+def test_shell_mass_fractions_sum_to_one(table10):
+    _, _, m = table10
+    assert m.sum() == pytest.approx(1.0, abs=1e-13)
+
+
+def test_second_moment_is_exact(table10):
+    # sum_i m_i q_i^2 = int q^4 f / int q^2 f, untruncated 15 zeta(5) / zeta(3)
+    _, q, m = table10
+    assert (m * q ** 2).sum() == pytest.approx(15.0 * ZETA5 / ZETA3, rel=1e-10)
+
+
+def test_first_moment_bounded_and_converging():
+    # Jensen: sum m_i q_i >= <q> = 7 pi^4 / (180 zeta(3)); approaches it as N_shell grows
+    mean_q = 7.0 * math.pi ** 4 / (180.0 * ZETA3)
+    errs = []
+    for ns in (5, 10, 40):
+        _, q, m = nu.shell_table(ns, [0.05] * 3)
+        first = (m * q).sum()
+        assert first >= mean_q
+        errs.append(first - mean_q)
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1.5e-2
+
+
+def test_equal_area_under_g_closed_form(table10):
+    # int_0^Q x/(e^x + 1) dx = Q^2/2 - Q ln(1 + e^Q) - Li2(-e^Q) + Li2(-1)  (independent of scipy)
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    edges, _, _ = table10
+
+    def G(Q):
+        Q = mp.mpf(Q)
+        return Q ** 2 / 2 - Q * mp.log(1 + mp.e ** Q) - mp.polylog(2, -mp.e ** Q) + mp.polylog(2, -1)
+    areas = [float(G(edges[i + 1]) - G(edges[i])) for i in range(10)]
+    total = float(G(edges[-1]))
+    for a in areas:
+        assert a == pytest.approx(total / 10.0, rel=1e-11)
+
+
+def test_shell_speed_and_mass_by_independent_quadrature(table10):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 25
+    edges, q, m = table10
+    f = lambda x: 1 / (mp.e ** x + 1)
+    z2 = mp.quad(lambda x: x ** 2 * f(x), [0, 5, 10, 40])
+    for i in (0, 4, 9):
+        lo, hi = edges[i], edges[i + 1]
+        pts = [lo, hi] if hi < 10 else [lo, 10, 20, hi]
+        m2 = mp.quad(lambda x: x ** 2 * f(x), pts)
+        m4 = mp.quad(lambda x: x ** 4 * f(x), pts)
+        assert q[i] == pytest.approx(float(mp.sqrt(m4 / m2)), rel=1e-11)
+        assert m[i] == pytest.approx(float(m2 / z2), rel=1e-11)
+
+
+def test_degenerate_limit_reduces_to_fermi_dirac():
+    # Eq. FD_deg: alpha_j -> 1 gives f~ = N_nu f, and the table does not depend on N_nu
+    a = nu.shell_table(6, [0.1])
+    b = nu.shell_table(6, [0.1, 0.1, 0.1])
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(x, y, rtol=1e-12)
+
+
+def test_effective_distribution_conserves_mass_and_second_moment():
+    # Appendix A: int q^2 f~ = 1.5 zeta(3) sum_j alpha_j, int q^4 f~ = 22.5 zeta(5) sum_j 1/alpha_j
+    masses = [0.12, 0.06, 0.02]
+    alphas = nu.mass_ratios(masses)
+    from scipy import integrate
+    ft = lambda q: nu.effective_fd(q, alphas)
+    z2, _ = integrate.quad(lambda q: q * q * ft(q), 0, 600, limit=800, epsrel=1e-13)
+    z4, _ = integrate.quad(lambda q: q ** 4 * ft(q), 0, 600, limit=800, epsrel=1e-13)
+    assert z2 == pytest.approx(1.5 * ZETA3 * sum(alphas), rel=1e-11)
+    assert z4 == pytest.approx(22.5 * ZETA5 * sum(1 / a for a in alphas), rel=1e-11)
+    # with q_max = 40 / alpha_min the table's second moment reproduces the ratio
+    _, q, m = nu.shell_table(10, masses, q_max=40.0 / min(alphas))
+    assert (m * q ** 2).sum() == pytest.approx(z4 / z2, rel=1e-9)
+
+
+def test_fibonacci_directions_symmetric_sums():
+    for nfib in (1, 3, 20):
+        d = nu.fibonacci_directions(nfib)
+        assert d.shape == (2 * nfib + 1, 3)
+        np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, rtol=1e-15)
+        assert abs(d[:, 2].sum()) < 1e-14          # sin(lat) antisymmetric in i
+        assert abs(d[:, 1].sum()) < 1e-14          # sin(lon) antisymmetric in i
+    # anisotropy of sum v v^T / n - I/3 is reported, bounded by O(1/N_fib) (parity unpinned)
+    d = nu.fibonacci_directions(20)
+    aniso = np.abs(d.T @ d / len(d) - np.eye(3) / 3).max()
+    assert aniso < 0.05
+
+
+def test_particle_counts_match_paper():
+    g = json.load(open(GOLDEN))
+    for row in g["table1"]["rows"]:
+        n_n = nu.neutrino_count(row["nsites"], row["nshell"], row["nfib"])
+        assert n_n == row["nsites"] ** 3 * row["nshell"] * (2 * row["nfib"] + 1)
+        assert row["nmesh"] == 2 * row["nc"]                      # Table 1: mesh twice the CDM grid
+    r = nu.neutrino_count(128, 10, 3) / 512 ** 3
+    assert round(r, g["nn_over_nc_nc512_nf3"]["printed_digits"] - 1) == g["nn_over_nc_nc512_nf3"]["value"]
+    r2 = nu.neutrino_count(128, 10, 25) / 1024 ** 3
+    assert round(r2, g["nn_over_nn_pseudo"]["printed_digits"]) == g["nn_over_nn_pseudo"]["value"]
+    kn = 2 * math.pi * g["k_n_hmpc"]["nsites"] / g["k_n_hmpc"]["box_mpc_h"]
+    assert round(kn, g["k_n_hmpc"]["printed_digits"]) == g["k_n_hmpc"]["value"]
+
+
+def test_species_masses_give_unit_mean_density():
+    _, _, m_shell = nu.shell_table(10, [0.2 / 3] * 3)
+    mc, mn = nu.species_masses(64, 32, 8, 10, 3, 0.3, 0.01, m_shell)
+    total = mc * 32 ** 3 + (mn * 7).sum() * 8 ** 3
+    assert total == pytest.approx(64.0 ** 3, rel=1e-14)
+    masses = nu.particle_masses(32 ** 3, 8 ** 3 * 70, 10, 3, mc, mn)
+    assert masses.sum() == pytest.approx(64.0 ** 3, rel=1e-13)
+
+
+def test_thermal_momentum_scale():
+    # q kT/(m c^2) c/H0 in Mpc/h; kT_nu0 = 1.6764e-4 eV for N_eff = 3 gives 7.54 per unit q at m = 0.2/3 eV
+    assert nu.thermal_momentum_scale(1.6764e-4, 0.2 / 3) == pytest.approx(7.54, rel=1e-3)
+
+
+def test_sites_are_staggered_from_cdm_lattice():
+    box, nc, ns = 64.0, 32, 8
+    s = nu.site_positions(ns, nc, box)
+    dc = box / nc
+    frac = (s / dc) % 1.0
+    assert np.all(np.abs(frac - 0.5) < 1e-12)        # half a CDM spacing off every lattice plane
