@@ -1,0 +1,235 @@
+/*
+ * pm.h -- C-ABI of libpmnu: a GB300 (sm_103a) particle-mesh step for CDM and
+ * quasi-randomly sampled massive-neutrino particles.
+ *
+ * Method: Bayer, Banerjee & Feng, "A fast particle-mesh simulation of
+ * non-linear cosmological structure formation with massive neutrinos"
+ * (arXiv 2007.13394).  The paper runs FastPM's particle-mesh solver with a
+ * kick-drift-kick integrator (§2.1 "Kick-Drift-Kick"; §2.3) whose growth-based
+ * kick and drift factors follow the Zel'dovich trajectory x = q + D(a) s;
+ * D(a) solves the growth ODE (§2.3 Eq. growthDE) on the background of
+ * Eq. Hubble; neutrinos are a second particle species that counts as matter
+ * in the Poisson source (§2.2 Eq. Om_pois); the force mesh is twice the CDM
+ * grid (§3, Table 1).  Neutrino particles come from N_shell Fermi-Dirac shells
+ * (§2.1 Eqs. q_shell, m_shell, N_shell, FD_deg) times 2 N_fib + 1 Fibonacci
+ * directions per site (Eq. N_n).
+ *
+ * Definitions the paper leaves to FastPM and that this library fixes:
+ *   positions   uint32 fixed point per axis, x = u L / 2^32, periodic by
+ *               integer wraparound;
+ *   paint       cloud-in-cell (CIC) of rho / rho_bar (mean 1) on an N^3 mesh,
+ *               deterministic (tile-local integer accumulation, no float atomics);
+ *   potential   phi_k = -(3/2) Omega_m0 delta_k / N^3 / (k^2 W(k)^2),
+ *               W = prod_d sinc^2(pi n_d / N), phi_0 = 0;
+ *   force       F_j = IFFT[-i k_j phi_k] with k_j = 0 on the Nyquist index,
+ *               read out with the paint's CIC weights;
+ *   kick/drift  p += K F, u += rne(Delta p 2^32 / L) (int32 wraparound), with
+ *               K1 = (g_p(a_h) - g_p(a_0)) / g_f(a_0),
+ *               Delta = (D(a_1) - D(a_0)) / g_p(a_h),
+ *               K2 = (g_p(a_1) - g_p(a_h)) / g_f(a_1),
+ *               g_p = a^3 E dD/da, g_f = 1.5 Omega_m0 D  (FP64 on the host).
+ *
+ * Units: box L in Mpc/h, H0 = 1; momentum p = a^2 (dx/dt) / H0 in Mpc/h; the
+ * mesh holds rho / rho_bar.  Particle masses follow from the particle id:
+ * id < n_cdm is CDM with mass (Omega_c0/Omega_m0) N^3 / n_c^3; a neutrino id
+ * n_cdm + (site * n_shell + shell) * (2 n_fib + 1) + dir has mass
+ * (Omega_nu0/Omega_m0) m_shell / (2 n_fib + 1) N^3 / n_sites^3 (units of the
+ * mean mass per mesh cell).
+ *
+ * Memory and ownership: every particle and output array passed in is owned
+ * by the caller; a context owns its scratch (two padded complex meshes of
+ * N * N * (N/2 + 2) float2 each, plus sort buffers for n_max particles).
+ * Arrays are structure-of-arrays: u[3 * n] holds the x plane, then y, then z.
+ * "Device" pointers are CUDA device memory of the context's device; "host"
+ * pointers are ordinary (preferably pinned) host memory.
+ *
+ * Streams and errors: calls taking a cudaStream_t (passed as void*, NULL =
+ * legacy default stream) enqueue work on it and return without waiting,
+ * except those documented as synchronous.  Every call returns an int status
+ * (PM_OK or a negative PM_E* code) and never aborts.  A kernel that detects a
+ * bad input (an out-of-range particle id, a bucket overflow) sets a device
+ * error word; synchronous calls and pm_sync() report it as PM_EKERNEL, and it
+ * stays set (sticky) until pm_sync() returns it.  A context is not
+ * thread-safe; use one per host thread.
+ */
+#ifndef PMNU_PM_H
+#define PMNU_PM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PM_OK = 0,
+  PM_EINVAL = -1,    /* bad argument (size, pointer, range, non power-of-two mesh) */
+  PM_ENOMEM = -2,    /* device or host allocation failed */
+  PM_ECUDA = -3,     /* a CUDA runtime call failed */
+  PM_EKERNEL = -4,   /* a kernel flagged bad input through the device error word */
+  PM_ETIMEOUT = -5,  /* a bounded device wait gave up */
+  PM_ENOTINIT = -6   /* null or destroyed context */
+};
+
+/* Species selectors for pm_paint and pm_power. */
+enum { PM_SPECIES_CDM = 1, PM_SPECIES_NU = 2, PM_SPECIES_ALL = 3 };
+
+/* Run configuration.  Zero-initialise, then set the fields. */
+typedef struct pm_config {
+  double box;          /* L, Mpc/h, > 0 */
+  int32_t nmesh;       /* N, power of two, 32 <= N <= 2048 (mesh twice the CDM grid in the paper) */
+  int32_t nc;          /* CDM lattice points per side (0: no CDM); nc <= N, N % nc == 0 for pm_ic */
+  int32_t nsites;      /* neutrino sites per side (0: no neutrinos); nc % nsites == 0 for pm_ic */
+  int32_t nshell;      /* Fermi-Dirac shells, >= 1 when nsites > 0 */
+  int32_t nfib;        /* Fibonacci parameter: 2 nfib + 1 directions per shell */
+  double h;            /* H0 / (100 km/s/Mpc) */
+  double omega_m;      /* total matter today, Omega_c0 + Omega_nu0 */
+  double t_cmb;        /* K; 0 selects 2.7255 */
+  double n_eff;        /* 0 selects 3.046 */
+  int32_t n_nu;        /* neutrino mass eigenstates in the background, 0..3 */
+  int32_t pad0;
+  double m_nu[3];      /* eigenstate masses in eV (M_nu = sum); heaviest sets the shell speeds */
+  double a_ini_ode;    /* start of the growth ODE; 0 selects 1/160 (z = 159, §2.3) */
+  int64_t n_max;       /* capacity of the sort scratch (>= every n passed later) */
+  double ns;           /* spectral index of the synthetic initial spectrum (pm_ic) */
+  double sigma8;       /* normalisation of the synthetic initial spectrum (pm_ic) */
+  uint32_t flags;      /* reserved, 0 */
+  int32_t pad1;
+} pm_config;
+
+/* Particle state.  All arrays are caller-owned device memory of length 3n (u, p, f)
+ * or n (id).  pm_step reorders every array in place into the library's tile order;
+ * id keeps each particle's canonical index.  f caches the force at a. */
+typedef struct pm_state {
+  uint32_t* u;
+  float* p;
+  uint32_t* id;
+  float* f;
+  int64_t n;
+  double a;
+  int32_t f_valid;
+  int32_t pad0;
+} pm_state;
+
+typedef struct pm_ctx pm_ctx;
+
+/* Human-readable text of a status code (static storage). */
+const char* pm_strerror(int status);
+
+/* ---- host-only FP64 helpers (no GPU needed) ------------------------------- */
+
+/* D(a) (normalised D(1) = 1), g_p(a), g_f(a), E(a) for the configured cosmology:
+ * growth ODE §2.3 Eq. growthDE with Omega_m(a) = Omega_m0 a^-3 / E^2, initial
+ * conditions D = dD/dln a = a_ini.  out[4] host.  Solves the ODE on every call. */
+int pm_cosmo_growth(const pm_config* cfg, double a, double* out);
+
+/* FastPM KDK factors for one step a0 -> a1 with half point ah: out[3] = {K1, Delta, K2}. */
+int pm_cosmo_coeffs(const pm_config* cfg, double a0, double ah, double a1, double* out);
+
+/* Fermi-Dirac shell table (§2.1 Eqs. N_shell, q_shell, m_shell with the effective
+ * distribution Eq. FD_deg over the configured masses): edges[nshell + 1],
+ * q_shell[nshell], m_shell[nshell], host arrays; q_max = 40. */
+int pm_nu_shells(const pm_config* cfg, double* edges, double* q_shell, double* m_shell);
+
+/* Background densities: out[5] = {Omega_gamma0, Omega_c0, Omega_nu0 (Poisson),
+ * Omega_Lambda, k_B T_nu0 in eV}. */
+int pm_cosmo_params(const pm_config* cfg, double* out);
+
+/* ---- context ----------------------------------------------------------------- */
+
+/* Validates cfg, builds the FP64 growth and shell tables, allocates the scratch on
+ * the current CUDA device.  *out receives the context; free it with pm_destroy. */
+int pm_init(const pm_config* cfg, pm_ctx** out);
+int pm_destroy(pm_ctx* ctx);
+
+/* Waits for the given stream, then returns PM_EKERNEL / PM_ETIMEOUT if a kernel set
+ * the device error word since the last pm_sync (and clears it), else PM_OK. */
+int pm_sync(pm_ctx* ctx, void* stream);
+
+/* Step coefficients from the context's tables: out[5] = {K1, Delta, K2, D(a0), D(a1)}. */
+int pm_coeffs(pm_ctx* ctx, double a0, double ah, double a1, double* out);
+
+/* ---- the particle-mesh path (device arrays, stream-ordered) ----------------- */
+
+/* Stable counting sort of particles into 16^3-cell tiles of the mesh.  key(i) =
+ * tile(i) * 8 + class(i): tile = (t_x (N/16) + t_y)(N/16) + t_z of the particle's
+ * cell, class = 4 [l_x = 15] + 2 [l_y = 15] + [l_z = 15] for its in-tile
+ * coordinates.  perm_out[k] = incoming index of the k-th particle in key order,
+ * ties in incoming order; key_out[k] its key (either output may be NULL). */
+int pm_sort(pm_ctx* ctx, const uint32_t* u, int64_t n, uint32_t* perm_out, uint32_t* key_out,
+            void* stream);
+
+/* CIC density rho / rho_bar of the selected species (PM_SPECIES_*) on the N^3 mesh.
+ * id may be NULL (particle i has id i).  mesh_out: device, N^3 floats, x-major
+ * with z fastest. */
+int pm_paint(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species,
+             float* mesh_out, void* stream);
+
+/* PM force at every particle, F_out[3 n] (device) in input order. */
+int pm_force(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, float* F_out,
+             void* stream);
+
+/* One kick-drift-kick step a0 -> a1 (ah <= 0 selects the arithmetic mean).  If
+ * st->f_valid is 0 the force at a0 is computed first.  On return the state holds
+ * (u, p, f) at a1 in tile order, st->a = a1, st->f_valid = 1. */
+int pm_step(pm_ctx* ctx, pm_state* st, double a0, double ah, double a1, void* stream);
+
+/* pm_step on HOST arrays (u[3n], p[3n], id[n], f[3n]): copies in, steps, copies out;
+ * synchronous.  *f_valid is read and updated.  Device state storage is allocated on
+ * first use and kept by the context. */
+int pm_step_host(pm_ctx* ctx, uint32_t* u, float* p, uint32_t* id, float* f, int64_t n,
+                 int32_t* f_valid, double a0, double ah, double a1, void* stream);
+
+/* Binned (cross) power spectrum of the species a and b (PM_SPECIES_*):
+ * P_ab(k) = (V / N^6) Re(delta_a delta_b^*) / W(k)^2, linear bins of width
+ * k_F = 2 pi / L from k_F / 2, mode-weighted mean |k|, r2c modes with
+ * 0 < n_z < N/2 counted twice.  Host outputs of length nbins (<= 2048);
+ * synchronous. */
+int pm_power(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species_a,
+             int32_t species_b, int32_t nbins, double* k_out, double* P_out, int64_t* nmodes_out,
+             void* stream);
+
+/* Zel'dovich initial conditions (stand-in for the paper's §2.2 REPS set-up): a BBKS
+ * spectrum normalised to cfg->sigma8 with index cfg->ns, from unit white noise
+ * noise[nc^3] (device, x-major).  CDM at lattice nodes i L / nc; neutrino sites at
+ * (i + 1/2) L / nsites + L / (2 nc), displaced by the same field (optionally
+ * suppressed by 1 / (1 + (k / k_fs)^2); k_fs <= 0 disables) evaluated exactly at the
+ * site, plus shell offsets 0.45 (L / nsites) q_shell / q_max,shell and thermal
+ * momenta q_shell k_B T_nu0 / m_heaviest (c / H0) along the Fibonacci directions.
+ * Writes st->u, st->p, st->id (canonical order), st->n, st->a = a0, st->f_valid = 0. */
+int pm_ic(pm_ctx* ctx, const float* noise, double a0, double k_fs, pm_state* st, void* stream);
+
+/* ---- stage-level entry points (device arrays; for testing each kernel) ------- */
+
+/* Forward r2c FFT (unnormalised, e^{-ikx}) of a real N^3 mesh: out holds
+ * N * N * (N/2 + 1) complex values as interleaved floats, kz fastest. */
+int pm_fft_r2c(pm_ctx* ctx, const float* mesh, float* out_complex, void* stream);
+/* Unnormalised inverse (e^{+ikx}) c2r of a Hermitian half spectrum, same layouts. */
+int pm_fft_c2r(pm_ctx* ctx, const float* in_complex, float* mesh_out, void* stream);
+/* phi_k of a density mesh: the r2c FFT with the Green's function fused into its
+ * last pass.  out_complex as in pm_fft_r2c. */
+int pm_potential(pm_ctx* ctx, const float* mesh, float* out_complex, void* stream);
+/* F_j mesh (j = 0, 1, 2) from phi_k: -i k_j fused into the first inverse pass. */
+int pm_force_mesh(pm_ctx* ctx, const float* phi_complex, int32_t component, float* mesh_out,
+                  void* stream);
+/* CIC readout of a real N^3 mesh at n particles: out[n]. */
+int pm_readout(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* mesh, float* out,
+               void* stream);
+
+/* ---- instrumentation --------------------------------------------------------- */
+
+/* Number of kernels this context has launched since pm_init. */
+int64_t pm_launch_count(pm_ctx* ctx);
+/* Enable (1) or disable (0) CUDA-event timing of every launch, per kernel kind. */
+int pm_profile_enable(pm_ctx* ctx, int32_t enable);
+/* Accumulated milliseconds and launches of kernel kind k (0 <= k < pm_kernel_kinds()),
+ * synchronous; resets the kind's counters when reset != 0. */
+int pm_profile_read(pm_ctx* ctx, int32_t kind, double* ms, int64_t* launches, int32_t reset);
+int32_t pm_kernel_kinds(void);
+const char* pm_kernel_name(int32_t kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMNU_PM_H */

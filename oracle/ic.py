@@ -132,7 +132,7 @@ def neutrino_particles(noise, box, pk, D0, gp0, n_sites, n_shell, n_fib, q_shell
     dc = box / nc
     r, j0, sh = neutrino_site_offset(nc, n_sites)
     s = displacement(delta_k(noise, box, pk), box, shift=sh * dc, k_fs=k_fs)
-    idx = j0 + r * np.arange(n_sites)
+    idx = (j0 + r * np.arange(n_sites)) % nc
     s_site = s[:, idx][:, :, idx][:, :, :, idx].reshape(3, -1)          # (3, n_sites^3)
     site = neutrinos.site_positions(n_sites, nc, box).T                  # (3, n_sites^3)
     dirs = neutrinos.fibonacci_directions(n_fib)                         # (ndir, 3)

@@ -21,7 +21,8 @@ GPU path is held to:
 * CIC readout of F_j at each particle with the paint's weights;
 * FastPM kick-drift-kick (§2.1 "Kick-Drift-Kick", §2.3) with the coefficients
   of :mod:`oracle.background`.
-* P_ab(k) = (V / N^6) Re(delta_a delta_b^*) / W(k)^2 per mode, no shot-noise
+* P_ab(k) = (V / N^6) Re(delta_a delta_b^*) / W(k)^2 per mode, each delta_s the
+  painted species over its own mean, no shot-noise
   subtraction, linear bins of width k_F = 2 pi / L starting at k_F / 2,
   mode-weighted mean |k| per bin, r2c modes with 0 < n_z < N/2 counted twice.
 
@@ -179,10 +180,13 @@ def kdk_step(u, p, f0, coeffs, mass, n, box, omega_m0):
 
 # ------------------------------------------------------------ power spectrum
 def power_spectrum(mesh_a, mesh_b, box, nbins):
-    """Binned P_ab(k); returns (k_mean, P, n_modes) of length nbins."""
+    """Binned P_ab(k) of delta_s = rho_s / rho_bar_s - 1 (each mesh over its own mean).
+
+    Returns (k_mean, P, n_modes) of length nbins.
+    """
     n = mesh_a.shape[0]
-    da = np.fft.rfftn(mesh_a)
-    db = da if mesh_b is None else np.fft.rfftn(mesh_b)
+    da = np.fft.rfftn(mesh_a / mesh_a.mean())
+    db = da if mesh_b is None else np.fft.rfftn(mesh_b / mesh_b.mean())
     kfull, khalf, _, nhalf = wavenumbers(n, box)
     wfull, whalf = cic_window(n)
     kmag = np.sqrt(kfull[:, None, None] ** 2 + kfull[None, :, None] ** 2 + khalf[None, None, :] ** 2)

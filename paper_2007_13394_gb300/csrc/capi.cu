@@ -1,0 +1,597 @@
+// C-ABI entry points of libpmnu (declared in include/pm.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pm_internal.cuh"
+
+using namespace pmnu;
+
+namespace pmnu {
+
+LaunchScope::LaunchScope(pm_ctx* ctx, cudaStream_t st, int k) : c(ctx), s(st), kind(k) {
+  ++c->launches;
+  if (c->prof) {
+    if (c->prof_pool.size() < 2) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      c->prof_pool.push_back(a);
+      c->prof_pool.push_back(b);
+    }
+    e1 = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    e0 = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    cudaEventRecord(e0, s);
+  }
+}
+
+LaunchScope::~LaunchScope() {
+  if (e0) {
+    cudaEventRecord(e1, s);
+    c->prof_live.push_back(Prof{kind, e0, e1});
+  }
+}
+
+float2* twiddles(pm_ctx* c, int n) {
+  auto it = c->tw.find(n);
+  if (it != c->tw.end()) return it->second;
+  std::vector<float2> h(n);
+  for (int t = 0; t < n; ++t) {
+    double a = -2.0 * 3.14159265358979323846 * t / n;
+    h[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  float2* d = nullptr;
+  if (cudaMalloc(&d, sizeof(float2) * n) != cudaSuccess) return nullptr;
+  cudaMemcpy(d, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+  c->tw[n] = d;
+  return d;
+}
+
+}  // namespace pmnu
+
+namespace {
+
+bool valid(pm_ctx* c) { return c && c->magic == kMagic; }
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+void drain_profile(pm_ctx* c) {
+  for (auto& p : c->prof_live) {
+    float ms = 0.f;
+    cudaEventSynchronize(p.b);
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    c->prof_ms[p.kind] += ms;
+    c->prof_n[p.kind] += 1;
+    c->prof_pool.push_back(p.a);
+    c->prof_pool.push_back(p.b);
+  }
+  c->prof_live.clear();
+}
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count) == cudaSuccess ? PM_OK : PM_ENOMEM;
+}
+
+void free_all(pm_ctx* c) {
+  cudaFree(c->meshA);
+  cudaFree(c->meshB);
+  for (auto& kv : c->tw) cudaFree(kv.second);
+  cudaFree(c->ksq);
+  cudaFree(c->winv);
+  cudaFree(c->kvec0);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(c->keys[i]);
+    cudaFree(c->vals[i]);
+  }
+  cudaFree(c->us);
+  cudaFree(c->ps);
+  cudaFree(c->ids);
+  cudaFree(c->counts);
+  cudaFree(c->bstart);
+  cudaFree(c->hist);
+  cudaFree(c->hist_scan);
+  cudaFree(c->scan_tmp);
+  cudaFree(c->pk_partial);
+  cudaFree(c->pk_final);
+  cudaFree(c->ic_amp);
+  cudaFree(c->ic_amp_nu);
+  cudaFree(c->err_dev);
+  if (c->err_host) cudaFreeHost(c->err_host);
+  cudaFree(c->hs_u);
+  cudaFree(c->hs_p);
+  cudaFree(c->hs_id);
+  cudaFree(c->hs_f);
+  for (auto& p : c->prof_live) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->prof_pool) cudaEventDestroy(e);
+}
+
+// sort (u, n) -> vals[0] = perm, keys[0] = sorted keys, bstart = bucket starts
+int sort_into_scratch(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
+  if (n > c->n_max) return PM_EINVAL;
+  return sort_particles(c, u, n, s);
+}
+
+// Paint of the sorted scratch particles into meshA (padded), then force component
+// meshes one at a time.  Callback per component with the real padded mesh in meshA.
+template <class F>
+int force_components(pm_ctx* c, int64_t n, cudaStream_t s, F&& per_comp) {
+  float* realA = reinterpret_cast<float*>(c->meshA);
+  paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, 2 * c->g.pc, s);
+  fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
+  for (int comp = 0; comp < 3; ++comp) {
+    fft_inverse_component(c, c->g, c->meshB, c->meshA, comp, s);
+    per_comp(comp, realA);
+  }
+  return PM_OK;
+}
+
+int check_state(pm_ctx* c, const pm_state* st) {
+  if (!st || st->n < 0 || st->n > c->n_max) return PM_EINVAL;
+  if (st->n > 0 && (!st->u || !st->p || !st->id || !st->f)) return PM_EINVAL;
+  return PM_OK;
+}
+
+int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStream_t s) {
+  int rc = check_state(c, st);
+  if (rc != PM_OK) return rc;
+  if (!(a0 > 0.0) || !(a1 > a0) || a1 > 2.0) return PM_EINVAL;
+  if (ah <= 0.0) ah = 0.5 * (a0 + a1);
+  if (!(ah >= a0 && ah <= a1)) return PM_EINVAL;
+  const int64_t n = st->n;
+  double k[3];
+  c->cosmo.coeffs(a0, ah, a1, k);
+  const float dscale = (float)(k[1] * 4294967296.0 / c->cfg.box);
+  if (!st->f_valid) {
+    // force at a0 on the current state (leaves the state in tile order)
+    rc = sort_into_scratch(c, st->u, n, s);
+    if (rc != PM_OK) return rc;
+    gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+    force_components(c, n, s, [&](int comp, float* mesh) {
+      readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, st->p, st->f,
+                   comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
+    });
+    st->f_valid = 1;
+  }
+  // first half kick + drift + keys of the drifted positions
+  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale, s);
+  rc = radix_and_buckets(c, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+  // force at a1 and the second half kick, written back in tile order
+  force_components(c, n, s, [&](int comp, float* mesh) {
+    readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, (float)k[2], st->p, st->f,
+                 comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
+  });
+  st->a = a1;
+  st->f_valid = 1;
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pm_strerror(int status) {
+  switch (status) {
+    case PM_OK: return "ok";
+    case PM_EINVAL: return "invalid argument";
+    case PM_ENOMEM: return "out of memory";
+    case PM_ECUDA: return "CUDA runtime error";
+    case PM_EKERNEL: return "a kernel flagged invalid input";
+    case PM_ETIMEOUT: return "a bounded device wait timed out";
+    case PM_ENOTINIT: return "context not initialised";
+    default: return "unknown status";
+  }
+}
+
+int pm_cosmo_growth(const pm_config* cfg, double a, double* out) {
+  if (!cfg || !out || !(a > 0.0) || a > 2.0) return PM_EINVAL;
+  Cosmo cm;
+  int rc = cm.init(*cfg);
+  if (rc != PM_OK) return rc;
+  out[0] = cm.D(a);
+  out[1] = cm.gp(a);
+  out[2] = cm.gf(a);
+  out[3] = cm.E(a);
+  return PM_OK;
+}
+
+int pm_cosmo_coeffs(const pm_config* cfg, double a0, double ah, double a1, double* out) {
+  if (!cfg || !out || !(a0 > 0.0) || !(a1 > a0) || a1 > 2.0 || ah < a0 || ah > a1) return PM_EINVAL;
+  Cosmo cm;
+  int rc = cm.init(*cfg);
+  if (rc != PM_OK) return rc;
+  cm.coeffs(a0, ah, a1, out);
+  return PM_OK;
+}
+
+int pm_cosmo_params(const pm_config* cfg, double* out) {
+  if (!cfg || !out) return PM_EINVAL;
+  Cosmo cm;
+  int rc = cm.init(*cfg);
+  if (rc != PM_OK) return rc;
+  out[0] = cm.omega_gamma;
+  out[1] = cm.omega_c;
+  out[2] = cm.omega_nu;
+  out[3] = cm.omega_lambda;
+  out[4] = cm.kT_nu0;
+  return PM_OK;
+}
+
+int pm_nu_shells(const pm_config* cfg, double* edges, double* q_shell, double* m_shell) {
+  if (!cfg || !edges || !q_shell || !m_shell) return PM_EINVAL;
+  int rc = validate_config(*cfg);
+  if (rc != PM_OK) return rc;
+  if (cfg->nshell < 1 || cfg->n_nu < 1) return PM_EINVAL;
+  return nu_shell_table(cfg->nshell, cfg->m_nu, cfg->n_nu, 40.0, edges, q_shell, m_shell);
+}
+
+int pm_init(const pm_config* cfg, pm_ctx** out) {
+  if (!cfg || !out) return PM_EINVAL;
+  *out = nullptr;
+  int rc = validate_config(*cfg);
+  if (rc != PM_OK) return rc;
+  if (cfg->nsites > 0 && cfg->nshell > kMaxShell) return PM_EINVAL;
+  pm_ctx* c = new (std::nothrow) pm_ctx();
+  if (!c) return PM_ENOMEM;
+  c->cfg = *cfg;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return PM_ECUDA;
+  }
+  rc = c->cosmo.init(*cfg);
+  if (rc != PM_OK) {
+    delete c;
+    return rc;
+  }
+  const int N = cfg->nmesh;
+  c->g.n = N;
+  c->g.logn = 0;
+  while ((1 << c->g.logn) < N) ++c->g.logn;
+  c->g.pc = N / 2 + 2;
+  c->nt = N / kTile;
+  c->ntl = c->g.logn - 4;
+  c->nbuckets = (long long)c->nt * c->nt * c->nt * 8;
+  int bits = 0;
+  while ((1LL << bits) < c->nbuckets) ++bits;
+  c->radix_passes = std::max(1, (bits + 7) / 8);
+  c->n_max = cfg->n_max;
+  if (c->n_max >= (int64_t)0xffffffffLL) {
+    delete c;
+    return PM_EINVAL;
+  }
+  // species masses (units of the mean mass per mesh cell)
+  const double cells = (double)N * N * N;
+  const double om = c->cosmo.omega_m0;
+  c->mt.n_cdm = (int64_t)cfg->nc * cfg->nc * cfg->nc;
+  c->m_cdm = cfg->nc > 0 ? c->cosmo.omega_c / om * cells / ((double)cfg->nc * cfg->nc * cfg->nc) : 0.0;
+  c->mt.m_cdm = (float)c->m_cdm;
+  c->mt.ndir = 2 * cfg->nfib + 1;
+  c->mt.nshell = cfg->nsites > 0 ? cfg->nshell : 1;
+  c->mt.n_nu = cfg->nsites > 0 ? (int64_t)cfg->nsites * cfg->nsites * cfg->nsites * cfg->nshell *
+                                     c->mt.ndir
+                               : 0;
+  if (cfg->nsites > 0) {
+    c->shell_edges.resize(cfg->nshell + 1);
+    c->q_shell.resize(cfg->nshell);
+    c->m_shell.resize(cfg->nshell);
+    rc = nu_shell_table(cfg->nshell, cfg->m_nu, cfg->n_nu, 40.0, c->shell_edges.data(),
+                        c->q_shell.data(), c->m_shell.data());
+    if (rc != PM_OK) {
+      delete c;
+      return rc;
+    }
+    c->m_nu.resize(cfg->nshell);
+    const double sites = (double)cfg->nsites * cfg->nsites * cfg->nsites;
+    for (int i = 0; i < cfg->nshell; ++i) {
+      c->m_nu[i] = c->cosmo.omega_nu / om * c->m_shell[i] / c->mt.ndir * cells / sites;
+      c->mt.m_nu[i] = (float)c->m_nu[i];
+    }
+  }
+  // device buffers
+  const size_t me = c->g.elems();
+  const int64_t nm = std::max<int64_t>(c->n_max, 1);
+  const long long hb = (nm + 4095) / 4096;
+  c->hist_blocks_max = hb;
+  const long long scan_n = std::max<long long>(256 * hb, c->nbuckets + 1);
+  {  // every level of the recursive scan keeps 2 * blocks words
+    size_t need = 64;
+    for (long long m = scan_n; m > 1; m = (m + 4095) / 4096) need += 2 * (size_t)((m + 4095) / 4096);
+    c->scan_tmp_elems = need;
+  }
+  if (dalloc(&c->meshA, me) || dalloc(&c->meshB, me) || dalloc(&c->ksq, N) ||
+      dalloc(&c->winv, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
+      dalloc(&c->keys[1], nm) || dalloc(&c->vals[0], nm) || dalloc(&c->vals[1], nm) ||
+      dalloc(&c->us, 3 * nm) || dalloc(&c->ps, 3 * nm) || dalloc(&c->ids, nm) ||
+      dalloc(&c->counts, c->nbuckets + 1) || dalloc(&c->bstart, c->nbuckets + 1) ||
+      dalloc(&c->hist, 256 * hb) || dalloc(&c->hist_scan, 256 * hb) ||
+      dalloc(&c->scan_tmp, c->scan_tmp_elems) || dalloc(&c->pk_partial, (size_t)N * 3 * 2048) ||
+      dalloc(&c->pk_final, 3 * 2048) || dalloc(&c->err_dev, 1)) {
+    free_all(c);
+    delete c;
+    return PM_ENOMEM;
+  }
+  if (cudaMallocHost(&c->err_host, sizeof(int)) != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return PM_ENOMEM;
+  }
+  cudaMemset(c->err_dev, 0, sizeof(int));
+  // k tables of the force mesh (FP64 on the host, stored as float)
+  {
+    std::vector<float> ksq(N), winv(N), kv(N);
+    const double kF = 2.0 * 3.14159265358979323846 / cfg->box;
+    for (int i = 0; i < N; ++i) {
+      int ns = i < N / 2 ? i : i - N;
+      double k = kF * ns;
+      double x = 3.14159265358979323846 * ns / N;
+      double sinc = ns == 0 ? 1.0 : std::sin(x) / x;
+      ksq[i] = (float)(k * k);
+      winv[i] = (float)(1.0 / std::pow(sinc, 4));
+      kv[i] = (i == N / 2) ? 0.0f : (float)k;
+    }
+    cudaMemcpy(c->ksq, ksq.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->winv, winv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->kvec0, kv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+  }
+  if (!twiddles(c, N)) {
+    free_all(c);
+    delete c;
+    return PM_ENOMEM;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return PM_ECUDA;
+  }
+  c->magic = kMagic;
+  *out = c;
+  return PM_OK;
+}
+
+int pm_destroy(pm_ctx* c) {
+  if (!valid(c)) return PM_ENOTINIT;
+  cudaDeviceSynchronize();
+  free_all(c);
+  c->magic = 0;
+  delete c;
+  return PM_OK;
+}
+
+int pm_sync(pm_ctx* c, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  cudaStream_t s = S(stream);
+  PM_CUDA_TRY(cudaMemcpyAsync(c->err_host, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaStreamSynchronize(s));
+  int e = *c->err_host;
+  if (e) {
+    cudaMemsetAsync(c->err_dev, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return (e & 2) ? PM_ETIMEOUT : PM_EKERNEL;
+  }
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_coeffs(pm_ctx* c, double a0, double ah, double a1, double* out) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!out || !(a0 > 0.0) || !(a1 > a0) || a1 > 2.0) return PM_EINVAL;
+  if (ah <= 0.0) ah = 0.5 * (a0 + a1);
+  if (ah < a0 || ah > a1) return PM_EINVAL;
+  c->cosmo.coeffs(a0, ah, a1, out);
+  out[3] = c->cosmo.D(a0);
+  out[4] = c->cosmo.D(a1);
+  return PM_OK;
+}
+
+int pm_sort(pm_ctx* c, const uint32_t* u, int64_t n, uint32_t* perm_out, uint32_t* key_out,
+            void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || (n > 0 && !u)) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  if (n > 0 && perm_out)
+    PM_CUDA_TRY(cudaMemcpyAsync(perm_out, c->vals[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  if (n > 0 && key_out)
+    PM_CUDA_TRY(cudaMemcpyAsync(key_out, c->keys[0], sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_paint(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species,
+             float* mesh_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || !mesh_out || (n > 0 && !u) || species < 1 || species > 3) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
+  paint_tiles(c, c->us, c->ids, n, species, mesh_out, c->g.n, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_force(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, float* F_out,
+             void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || (n > 0 && (!u || !F_out))) return PM_EINVAL;
+  if (n == 0) return PM_OK;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
+  force_components(c, n, s, [&](int comp, float* mesh) {
+    readout_kick(c, c->us, nullptr, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, nullptr, F_out,
+                 nullptr, nullptr, c->vals[0], s);
+  });
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_step(pm_ctx* c, pm_state* st, double a0, double ah, double a1, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  return step_impl(c, st, a0, ah, a1, S(stream));
+}
+
+int pm_step_host(pm_ctx* c, uint32_t* u, float* p, uint32_t* id, float* f, int64_t n,
+                 int32_t* f_valid, double a0, double ah, double a1, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n <= 0 || n > c->n_max || !u || !p || !id || !f || !f_valid) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  if (n > c->hs_cap) {
+    cudaFree(c->hs_u);
+    cudaFree(c->hs_p);
+    cudaFree(c->hs_id);
+    cudaFree(c->hs_f);
+    c->hs_u = nullptr;
+    c->hs_p = c->hs_f = nullptr;
+    c->hs_id = nullptr;
+    c->hs_cap = 0;
+    if (dalloc(&c->hs_u, 3 * n) || dalloc(&c->hs_p, 3 * n) || dalloc(&c->hs_id, n) ||
+        dalloc(&c->hs_f, 3 * n))
+      return PM_ENOMEM;
+    c->hs_cap = n;
+  }
+  PM_CUDA_TRY(cudaMemcpyAsync(c->hs_u, u, 12 * n, cudaMemcpyHostToDevice, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(c->hs_p, p, 12 * n, cudaMemcpyHostToDevice, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(c->hs_id, id, 4 * n, cudaMemcpyHostToDevice, s));
+  if (*f_valid) PM_CUDA_TRY(cudaMemcpyAsync(c->hs_f, f, 12 * n, cudaMemcpyHostToDevice, s));
+  pm_state st{c->hs_u, c->hs_p, c->hs_id, c->hs_f, n, a0, *f_valid, 0};
+  int rc = step_impl(c, &st, a0, ah, a1, s);
+  if (rc != PM_OK) return rc;
+  PM_CUDA_TRY(cudaMemcpyAsync(u, c->hs_u, 12 * n, cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(p, c->hs_p, 12 * n, cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(id, c->hs_id, 4 * n, cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(f, c->hs_f, 12 * n, cudaMemcpyDeviceToHost, s));
+  *f_valid = st.f_valid;
+  return pm_sync(c, stream);
+}
+
+int pm_power(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, int32_t sa, int32_t sb,
+             int32_t nbins, double* k_out, double* P_out, int64_t* nmodes_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || (n > 0 && !u) || sa < 1 || sa > 3 || sb < 1 || sb > 3 || !k_out || !P_out ||
+      !nmodes_out)
+    return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
+  float* realA = reinterpret_cast<float*>(c->meshA);
+  float* realB = reinterpret_cast<float*>(c->meshB);
+  paint_tiles(c, c->us, c->ids, n, sa, realA, 2 * c->g.pc, s);
+  fft_forward(c, c->g, c->meshA, c->meshA, 0, s);
+  const float2* db = c->meshA;
+  if (sb != sa) {
+    paint_tiles(c, c->us, c->ids, n, sb, realB, 2 * c->g.pc, s);
+    fft_forward(c, c->g, c->meshB, c->meshB, 0, s);
+    db = c->meshB;
+  }
+  rc = power_bin(c, c->meshA, db, nbins, k_out, P_out, nmodes_out, s);
+  if (rc != PM_OK) return rc;
+  return pm_sync(c, stream);
+}
+
+int pm_ic(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!noise || !st || !st->u || !st->p || !st->id) return PM_EINVAL;
+  return ic_build(c, noise, a0, k_fs, st, S(stream));
+}
+
+int pm_fft_r2c(pm_ctx* c, const float* mesh, float* out_complex, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!mesh || !out_complex) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  repack_real(c, c->g, mesh, c->g.n, reinterpret_cast<float*>(c->meshA), 2 * c->g.pc, s);
+  fft_forward(c, c->g, c->meshA, c->meshA, 0, s);
+  repack_complex(c, c->g, c->meshA, c->g.pc, reinterpret_cast<float2*>(out_complex),
+                 c->g.n / 2 + 1, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_fft_c2r(pm_ctx* c, const float* in_complex, float* mesh_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!in_complex || !mesh_out) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  repack_complex(c, c->g, reinterpret_cast<const float2*>(in_complex), c->g.n / 2 + 1, c->meshA,
+                 c->g.pc, s);
+  fft_inverse_plain(c, c->g, c->meshA, s);
+  repack_real(c, c->g, reinterpret_cast<float*>(c->meshA), 2 * c->g.pc, mesh_out, c->g.n, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_potential(pm_ctx* c, const float* mesh, float* out_complex, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!mesh || !out_complex) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  repack_real(c, c->g, mesh, c->g.n, reinterpret_cast<float*>(c->meshA), 2 * c->g.pc, s);
+  fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
+  repack_complex(c, c->g, c->meshB, c->g.pc, reinterpret_cast<float2*>(out_complex),
+                 c->g.n / 2 + 1, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_force_mesh(pm_ctx* c, const float* phi_complex, int32_t comp, float* mesh_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!phi_complex || !mesh_out || comp < 0 || comp > 2) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  repack_complex(c, c->g, reinterpret_cast<const float2*>(phi_complex), c->g.n / 2 + 1, c->meshB,
+                 c->g.pc, s);
+  fft_inverse_component(c, c->g, c->meshB, c->meshA, comp, s);
+  repack_real(c, c->g, reinterpret_cast<float*>(c->meshA), 2 * c->g.pc, mesh_out, c->g.n, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_readout(pm_ctx* c, const uint32_t* u, int64_t n, const float* mesh, float* out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || (n > 0 && (!u || !mesh || !out))) return PM_EINVAL;
+  if (n == 0) return PM_OK;
+  cudaStream_t s = S(stream);
+  // readout of a contiguous (row pitch N) mesh in input order
+  readout_kick(c, u, nullptr, nullptr, n, mesh, c->g.n, 0, 0.0f, nullptr, out, nullptr, nullptr,
+               nullptr, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int64_t pm_launch_count(pm_ctx* c) { return valid(c) ? c->launches : -1; }
+
+int pm_profile_enable(pm_ctx* c, int32_t enable) {
+  if (!valid(c)) return PM_ENOTINIT;
+  c->prof = enable != 0;
+  return PM_OK;
+}
+
+int pm_profile_read(pm_ctx* c, int32_t kind, double* ms, int64_t* launches, int32_t reset) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (kind < 0 || kind >= K_NUM_KINDS || !ms || !launches) return PM_EINVAL;
+  drain_profile(c);
+  *ms = c->prof_ms[kind];
+  *launches = c->prof_n[kind];
+  if (reset) {
+    c->prof_ms[kind] = 0.0;
+    c->prof_n[kind] = 0;
+  }
+  return PM_OK;
+}
+
+int32_t pm_kernel_kinds(void) { return K_NUM_KINDS; }
+
+const char* pm_kernel_name(int32_t k) {
+  static const char* names[K_NUM_KINDS] = {
+      "keys",          "scan",         "radix_hist",   "radix_scatter",   "gather",
+      "paint_tiles",   "fft_z_r2c",    "fft_y",        "fft_x_green",     "fft_x_grad",
+      "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
+      "power_reduce",  "ic_za",        "ic_assemble",  "repack"};
+  if (k < 0 || k >= K_NUM_KINDS) return "unknown";
+  return names[k];
+}
+
+}  // extern "C"

@@ -1,0 +1,420 @@
+// 3D real FFT of the padded mesh, built from three axis passes.
+//
+// Layout: complex mesh C[x][y][kz], kz in [0, N/2], row pitch P = N/2 + 2 float2
+// (the same bytes as a real mesh with row pitch 2P floats, so every pass can run
+// in place).  Forward: z pass r2c (rows of N reals -> N/2 + 1 complex), y pass
+// c2c, x pass c2c with the Green's function multiply fused into its epilogue
+// (written to a second buffer).  Inverse for force component j: x pass with the
+// -i k_j multiply fused into its prologue (second buffer -> first), y pass, z
+// pass c2r.
+//
+// Each line of M points is held by M/16 threads, 16 values each (value s of
+// thread j is element j + s M/16).  Stockham stages of radix 16 (the last stage
+// radix 2..16) run in registers; between stages the line goes through shared
+// memory, padded by one float2 per 16 to keep the stride-16 writes free of bank
+// conflicts.  The first stage reads global memory directly and the last stage
+// writes it directly, both coalesced.  Twiddles come from a table
+// e^{-2 pi i t / N} computed in double precision on the host.
+//
+// The strided passes (y, x) put TK adjacent kz columns in one CTA, lane-fastest,
+// so each global access covers TK consecutive float2.
+#include <cuda_runtime.h>
+
+#include "pm_internal.cuh"
+
+namespace pmnu {
+
+namespace {
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// e^{s 2 pi i m / 16} for compile-time m, s = -1 forward, +1 inverse
+template <int m, bool INV>
+__device__ __forceinline__ float2 w16() {
+  constexpr float C[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                           0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                           -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                           0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  constexpr float cv = C[m & 15];
+  constexpr float sv = C[(m + 12) & 15];  // sin(2 pi m / 16) = cos(2 pi (m - 4) / 16)
+  return INV ? make_float2(cv, sv) : make_float2(cv, -sv);
+}
+
+template <int m, bool INV>
+__device__ __forceinline__ float2 rot16(float2 a) {
+  if constexpr ((m & 15) == 0) {
+    return a;
+  } else if constexpr ((m & 15) == 4) {  // multiply by -i (forward) or +i (inverse)
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  } else if constexpr ((m & 15) == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr ((m & 15) == 12) {
+    return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+  } else {
+    return cmul(a, w16<m, INV>());
+  }
+}
+
+template <int R>
+__host__ __device__ constexpr int brev(int i) {
+  int r = 0;
+  for (int b = 1, k = R >> 1; b < R; b <<= 1, k >>= 1)
+    if (i & b) r |= k;
+  return r;
+}
+
+// In-register DFT of size R (2, 4, 8, 16): radix-2 decimation in time.
+template <int R, bool INV, int LEN = 2>
+__device__ __forceinline__ void dft_layers(float2 (&x)[R]);
+
+template <int R, bool INV, int LEN, int I, int K>
+__device__ __forceinline__ void dft_bfly(float2 (&x)[R]) {
+  if constexpr (I < R) {
+    if constexpr (K < LEN / 2) {
+      float2 a = x[I + K];
+      float2 b = rot16<K * (16 / LEN), INV>(x[I + K + LEN / 2]);
+      x[I + K] = cadd(a, b);
+      x[I + K + LEN / 2] = csub(a, b);
+      dft_bfly<R, INV, LEN, I, K + 1>(x);
+    } else {
+      dft_bfly<R, INV, LEN, I + LEN, 0>(x);
+    }
+  }
+}
+
+template <int R, bool INV, int LEN>
+__device__ __forceinline__ void dft_layers(float2 (&x)[R]) {
+  if constexpr (LEN <= R) {
+    dft_bfly<R, INV, LEN, 0, 0>(x);
+    dft_layers<R, INV, LEN * 2>(x);
+  }
+}
+
+template <int R, int I>
+__device__ __forceinline__ void bitrev_perm(float2 (&x)[R]) {
+  if constexpr (I < R) {
+    constexpr int J = brev<R>(I);
+    if constexpr (J > I) {
+      float2 t = x[I];
+      x[I] = x[J];
+      x[J] = t;
+    }
+    bitrev_perm<R, I + 1>(x);
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+  bitrev_perm<R, 0>(x);
+  dft_layers<R, INV, 2>(x);
+}
+
+// One Stockham stage on a line of M points (sub-transform length NS, radix R).
+template <int M, int TWN, int NS, int R, bool INV, bool LAST>
+__device__ __forceinline__ void stage(float2 (&v)[16], int j, float2* sm, int cs,
+                                      const float2* __restrict__ tw) {
+  constexpr int B = 16 / R;  // butterflies per thread
+  constexpr int Q = M / 16;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int jj = j + b * Q;
+    const int k = jj & (NS - 1);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[b + r * B];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(tw + ((k * r * (TWN / (NS * R))) & (TWN - 1)));
+        x[r] = cmul(x[r], INV ? cconj(w) : w);
+      }
+    }
+    dft<R, INV>(x);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * B] = x[r];
+    } else {
+      const int base = (jj / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    __syncthreads();
+  }
+}
+
+template <int M, int TWN, int NS, bool INV>
+__device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, int cs,
+                                           const float2* __restrict__ tw) {
+  constexpr int REM = M / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr bool LAST = (NS * R == M);
+  stage<M, TWN, NS, R, INV, LAST>(v, j, sm, cs, tw);
+  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV>(v, j, sm, cs, tw);
+}
+
+constexpr int kZThreads = 256;
+
+// z pass, real -> complex, in place on rows of pitch P float2.
+template <int LOGN>
+__global__ void __launch_bounds__(kZThreads) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
+                                                         int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
+  constexpr int LS = M + M / 16 + 2;  // line stride in shared memory
+  extern __shared__ float2 sm[];
+  const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+  const long long row = (long long)blockIdx.x * LPC + line;
+  const bool ok = row < nrows;
+  float2* rp = data + row * pc;
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = ok ? rp[j + s * TPL] : make_float2(0.f, 0.f);
+  float2* ls = sm + line * LS;
+  run_stages<M, N, 1, false>(v, j, ls, 1, tw);
+#pragma unroll
+  for (int s = 0; s < 16; ++s) ls[padi(j + s * TPL)] = v[s];
+  __syncthreads();
+  if (!ok) return;
+  for (int k = j; k <= M; k += TPL) {
+    float2 zk = ls[padi(k & (M - 1))];
+    float2 zm = cconj(ls[padi((M - k) & (M - 1))]);
+    float2 e = cscale(cadd(zk, zm), 0.5f);
+    float2 o = cscale(csub(zk, zm), 0.5f);
+    float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
+    float2 wo = cmul(w, o);
+    rp[k] = make_float2(e.x + wo.y, e.y - wo.x);  // e - i w o
+  }
+}
+
+// z pass, complex -> real, in place.
+template <int LOGN>
+__global__ void __launch_bounds__(kZThreads) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
+                                                         int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
+  constexpr int LS = M + M / 16 + 2;
+  extern __shared__ float2 sm[];
+  const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
+  const long long row = (long long)blockIdx.x * LPC + line;
+  const bool ok = row < nrows;
+  float2* rp = data + row * pc;
+  float2* ls = sm + line * LS;
+  for (int k = j; k <= M; k += TPL) ls[padi(k)] = ok ? rp[k] : make_float2(0.f, 0.f);
+  __syncthreads();
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int k = j + s * TPL;
+    float2 xk = ls[padi(k)];
+    float2 xm = cconj(ls[padi(M - k)]);
+    float2 e = cadd(xk, xm);
+    float2 d = csub(xk, xm);
+    float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
+    float2 wd = cmul(w, d);
+    v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
+  }
+  __syncthreads();
+  run_stages<M, N, 1, true>(v, j, ls, 1, tw);
+  if (!ok) return;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
+}
+
+// Fused epilogue / prologue of the x pass.
+struct KTables {
+  const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)
+  const float* winv;   // 1 / sinc^4(pi n_s / N)
+  const float* kvec0;  // k_n with the Nyquist index set to 0
+  float gcoef;         // -1.5 Omega_m0 / N^3
+};
+
+enum { EPI_NONE = 0, EPI_GREEN = 1 };
+enum { PRO_NONE = 0, PRO_GRAD = 1 };
+
+// Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK).
+template <int LOGM, int TK, bool INV, int EPI, int PRO>
+__global__ void __launch_bounds__(TK*(1 << LOGM) / 16) k_fft_strided(
+    const float2* __restrict__ src, float2* __restrict__ dst, int axis, int pc, int ntiles_z,
+    const float2* __restrict__ tw, KTables kt, int comp) {
+  constexpr int M = 1 << LOGM, Q = M / 16;
+  extern __shared__ float2 sm[];
+  const int c = threadIdx.x % TK, j = threadIdx.x / TK;
+  const int outer = blockIdx.x / ntiles_z;
+  const int kz = (blockIdx.x % ntiles_z) * TK + c;
+  const bool ok = kz <= M / 2;
+  const long long stride = axis == 1 ? (long long)pc : (long long)M * pc;
+  const long long base = (axis == 1 ? (long long)outer * M * pc : (long long)outer * pc) + kz;
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s)
+    v[s] = ok ? src[base + (long long)(j + s * Q) * stride] : make_float2(0.f, 0.f);
+  if constexpr (PRO == PRO_GRAD) {  // v *= -i k_comp; x pass: element index is kx, outer is ky
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int kx = j + s * Q;
+      const float kk = comp == 0 ? __ldg(kt.kvec0 + kx)
+                                 : (comp == 1 ? __ldg(kt.kvec0 + outer) : __ldg(kt.kvec0 + kz));
+      v[s] = make_float2(kk * v[s].y, -kk * v[s].x);
+    }
+  }
+  run_stages<M, M, 1, INV>(v, j, sm + c, TK, tw);
+  if constexpr (EPI == EPI_GREEN) {
+    const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
+    const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int kx = j + s * Q;
+      const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
+      float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
+      if (k2 == 0.0f) g = 0.0f;
+      v[s] = cscale(v[s], g);
+    }
+  }
+  if (!ok) return;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) dst[base + (long long)(j + s * Q) * stride] = v[s];
+}
+
+template <int LOGM>
+constexpr int tk_for() {
+  return LOGM >= 11 ? 4 : (LOGM == 10 ? 8 : 16);
+}
+
+template <int LOGM, bool INV, int EPI, int PRO>
+void launch_strided(const float2* src, float2* dst, int axis, int pc, const float2* tw,
+                    const KTables& kt, int comp, cudaStream_t s) {
+  constexpr int M = 1 << LOGM, TK = tk_for<LOGM>();
+  constexpr int threads = TK * M / 16;
+  const int ntz = (M / 2 + 1 + TK - 1) / TK;
+  const size_t smem = sizeof(float2) * (size_t)(M + M / 16 + 1) * TK;
+  auto kern = k_fft_strided<LOGM, TK, INV, EPI, PRO>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  kern<<<(unsigned)(M * ntz), threads, smem, s>>>(src, dst, axis, pc, ntz, tw, kt, comp);
+}
+
+template <int LOGN>
+void launch_z(float2* data, long long nrows, int pc, const float2* tw, bool inverse, cudaStream_t s) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
+  constexpr int LS = M + M / 16 + 2;
+  const size_t smem = sizeof(float2) * (size_t)LS * LPC;
+  unsigned grid = (unsigned)((nrows + LPC - 1) / LPC);
+  if (inverse) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_fft_z_c2r<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    k_fft_z_c2r<LOGN><<<grid, kZThreads, smem, s>>>(data, nrows, pc, tw);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_fft_z_r2c<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    k_fft_z_r2c<LOGN><<<grid, kZThreads, smem, s>>>(data, nrows, pc, tw);
+  }
+}
+
+void dispatch_z(const Geom& g, float2* data, const float2* tw, bool inverse, cudaStream_t s) {
+  switch (g.logn) {
+    case 5: launch_z<5>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 6: launch_z<6>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 7: launch_z<7>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 8: launch_z<8>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 9: launch_z<9>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 10: launch_z<10>(data, g.rows(), g.pc, tw, inverse, s); break;
+    case 11: launch_z<11>(data, g.rows(), g.pc, tw, inverse, s); break;
+    default: break;
+  }
+}
+
+template <bool INV, int EPI, int PRO>
+void dispatch_strided(const Geom& g, const float2* src, float2* dst, int axis, const float2* tw,
+                      const KTables& kt, int comp, cudaStream_t s) {
+  switch (g.logn) {
+    case 5: launch_strided<5, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 6: launch_strided<6, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 7: launch_strided<7, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 8: launch_strided<8, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 9: launch_strided<9, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 10: launch_strided<10, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    case 11: launch_strided<11, INV, EPI, PRO>(src, dst, axis, g.pc, tw, kt, comp, s); break;
+    default: break;
+  }
+}
+
+KTables ktables(pm_ctx* c, const Geom& g) {
+  KTables kt;
+  kt.ksq = c->ksq;
+  kt.winv = c->winv;
+  kt.kvec0 = c->kvec0;
+  double nn = (double)g.n;
+  kt.gcoef = (float)(-1.5 * c->cosmo.omega_m0 / (nn * nn * nn));
+  return kt;
+}
+
+}  // namespace
+
+void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, cudaStream_t s) {
+  const float2* tw = twiddles(c, g.n);
+  KTables kt = ktables(c, g);
+  {
+    LaunchScope L(c, s, K_FFT_Z_R2C);
+    dispatch_z(g, buf, tw, false, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+  }
+  if (green) {
+    LaunchScope L(c, s, K_FFT_X_GREEN);
+    dispatch_strided<false, EPI_GREEN, PRO_NONE>(g, buf, dst, 0, tw, kt, 0, s);
+  } else {
+    LaunchScope L(c, s, K_FFT_X_PLAIN);
+    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, buf, dst, 0, tw, kt, 0, s);
+  }
+}
+
+void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* buf, int comp,
+                           cudaStream_t s) {
+  const float2* tw = twiddles(c, g.n);
+  KTables kt = ktables(c, g);
+  {
+    LaunchScope L(c, s, K_FFT_X_GRAD);
+    dispatch_strided<true, EPI_NONE, PRO_GRAD>(g, phi, buf, 0, tw, kt, comp, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Z_C2R);
+    dispatch_z(g, buf, tw, true, s);
+  }
+}
+
+void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s) {
+  const float2* tw = twiddles(c, g.n);
+  KTables kt = ktables(c, g);
+  {
+    LaunchScope L(c, s, K_FFT_X_PLAIN);
+    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 0, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Z_C2R);
+    dispatch_z(g, buf, tw, true, s);
+  }
+}
+
+}  // namespace pmnu

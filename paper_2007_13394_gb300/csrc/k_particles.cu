@@ -1,0 +1,239 @@
+// Particle <-> mesh kernels: deterministic tile paint, CIC readout fused with the
+// kick, the first kick fused with the drift and the next sort keys.
+//
+// Paint (CIC of rho / rho_bar): one CTA per 16^3 tile.  The tile's own particles
+// are the bucket range [bstart[8 t], bstart[8 t + 8]); a particle on the tile's
+// high face layer (class bits) also reaches the neighbouring tile, which reads
+// exactly those classes of its seven low-side neighbours.  Each (particle,
+// corner) pair is therefore counted by the one CTA that owns the corner cell.
+// Contributions are accumulated in shared memory as 64-bit fixed point
+// (2^-32 resolution): integer addition is associative, so the result does not
+// depend on thread scheduling, and no global float atomics are used.
+#include <cuda_runtime.h>
+
+#include "pm_internal.cuh"
+
+namespace pmnu {
+
+namespace {
+
+constexpr int kPaintThreads = 256;
+constexpr int kTileCells = kTile * kTile * kTile;  // 4096
+constexpr float kFix = 4294967296.0f;              // 2^32
+constexpr float kUnfix = 2.3283064365386963e-10f;  // 2^-32
+
+__device__ __forceinline__ void paint_one(long long* acc, uint32_t ux, uint32_t uy, uint32_t uz,
+                                          float m, int shift, int n, int ox, int oy, int oz,
+                                          float fscale, uint32_t fmask) {
+  int c[3] = {(int)(ux >> shift), (int)(uy >> shift), (int)(uz >> shift)};
+  int o[3] = {ox, oy, oz};
+  float f[3] = {(float)(ux & fmask) * fscale, (float)(uy & fmask) * fscale,
+                (float)(uz & fmask) * fscale};
+  int l[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int v = c[d] - o[d];  // local coordinate relative to the tile origin
+    if (v > n / 2) v -= n;
+    if (v < -n / 2) v += n;
+    l[d] = v;
+  }
+#pragma unroll
+  for (int bx = 0; bx < 2; ++bx) {
+    int lx = l[0] + bx;
+    if (lx < 0 || lx >= kTile) continue;
+    float wx = bx ? f[0] : 1.0f - f[0];
+#pragma unroll
+    for (int by = 0; by < 2; ++by) {
+      int ly = l[1] + by;
+      if (ly < 0 || ly >= kTile) continue;
+      float wxy = wx * (by ? f[1] : 1.0f - f[1]);
+#pragma unroll
+      for (int bz = 0; bz < 2; ++bz) {
+        int lz = l[2] + bz;
+        if (lz < 0 || lz >= kTile) continue;
+        float w = wxy * (bz ? f[2] : 1.0f - f[2]) * m;
+        long long q = __float2ll_rn(w * kFix);
+        atomicAdd((unsigned long long*)&acc[(lx * kTile + ly) * kTile + lz], (unsigned long long)q);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
+    const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
+    const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
+    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err) {
+  __shared__ long long acc[kTileCells];
+  const int t = threadIdx.x;
+  for (int i = t; i < kTileCells; i += kPaintThreads) acc[i] = 0;
+  __syncthreads();
+  const int nt = 1 << ntl;
+  const uint32_t tile = blockIdx.x;
+  const int tx = tile >> (2 * ntl), ty = (tile >> ntl) & (nt - 1), tz = tile & (nt - 1);
+  const float fscale = 1.0f / (float)(1u << shift);
+  const uint32_t fmask = (1u << shift) - 1u;
+  bool bad = false;
+  // o = 0: own tile (all classes); o = 1..7: low-side neighbour along the set bits,
+  // classes that contain every bit of o
+  for (int o = 0; o < 8; ++o) {
+    const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+    const uint32_t nb = ((uint32_t)((tx - ox) & (nt - 1)) << (2 * ntl)) |
+                        ((uint32_t)((ty - oy) & (nt - 1)) << ntl) | (uint32_t)((tz - oz) & (nt - 1));
+    for (int cls = 0; cls < 8; ++cls) {
+      if ((cls & o) != o) continue;
+      uint32_t lo = bstart[nb * 8 + cls], hi;
+      if (o == 0) {  // own tile: one contiguous run over all classes
+        hi = bstart[nb * 8 + 8];
+        cls = 8;
+      } else {
+        hi = bstart[nb * 8 + cls + 1];
+      }
+      for (uint32_t k = lo + t; k < hi; k += kPaintThreads) {
+        float m = id_mass(mt, ids[k], species, &bad);
+        if (m == 0.0f) continue;
+        paint_one(acc, us[k], us[n + k], us[2 * n + k], m, shift, nm, tx * kTile, ty * kTile,
+                  tz * kTile, fscale, fmask);
+      }
+    }
+  }
+  if (bad) atomicOr(err, 1);
+  __syncthreads();
+  // write the tile: 256 rows of 16 floats, as float4
+  for (int q = t; q < kTileCells / 4; q += kPaintThreads) {
+    int row = q >> 2, z4 = (q & 3) * 4;
+    int lx = row >> 4, ly = row & 15;
+    const long long* a = &acc[(lx * kTile + ly) * kTile + z4];
+    float4 v = make_float4(__ll2float_rn(a[0]) * kUnfix, __ll2float_rn(a[1]) * kUnfix,
+                           __ll2float_rn(a[2]) * kUnfix, __ll2float_rn(a[3]) * kUnfix);
+    size_t off = ((size_t)(tx * kTile + lx) * nm + (ty * kTile + ly)) * (size_t)row_pitch +
+                 tz * kTile + z4;
+    *reinterpret_cast<float4*>(mesh + off) = v;
+  }
+}
+
+// CIC readout of one real mesh component fused with the kick p_j += K F_j.
+__global__ void k_readout_kick(const uint32_t* __restrict__ us, const float* __restrict__ ps,
+                               const uint32_t* __restrict__ ids, int64_t n,
+                               const float* __restrict__ mesh, int nm, int shift, int row_pitch,
+                               int comp, float K, float* __restrict__ p_out,
+                               float* __restrict__ f_out, uint32_t* __restrict__ u_out,
+                               uint32_t* __restrict__ id_out, const uint32_t* __restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t ux = us[i], uy = us[n + i], uz = us[2 * n + i];
+  const float fscale = 1.0f / (float)(1u << shift);
+  const uint32_t fmask = (1u << shift) - 1u;
+  const int cx = ux >> shift, cy = uy >> shift, cz = uz >> shift;
+  const int cx1 = (cx + 1) & (nm - 1), cy1 = (cy + 1) & (nm - 1), cz1 = (cz + 1) & (nm - 1);
+  const float fx = (float)(ux & fmask) * fscale, fy = (float)(uy & fmask) * fscale,
+              fz = (float)(uz & fmask) * fscale;
+  const size_t r00 = ((size_t)cx * nm + cy) * row_pitch, r01 = ((size_t)cx * nm + cy1) * row_pitch;
+  const size_t r10 = ((size_t)cx1 * nm + cy) * row_pitch, r11 = ((size_t)cx1 * nm + cy1) * row_pitch;
+  const float v000 = __ldg(mesh + r00 + cz), v001 = __ldg(mesh + r00 + cz1);
+  const float v010 = __ldg(mesh + r01 + cz), v011 = __ldg(mesh + r01 + cz1);
+  const float v100 = __ldg(mesh + r10 + cz), v101 = __ldg(mesh + r10 + cz1);
+  const float v110 = __ldg(mesh + r11 + cz), v111 = __ldg(mesh + r11 + cz1);
+  const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+  const float F = gx * (gy * (gz * v000 + fz * v001) + fy * (gz * v010 + fz * v011)) +
+                  fx * (gy * (gz * v100 + fz * v101) + fy * (gz * v110 + fz * v111));
+  if (perm) {  // stage-level readout / force in the caller's order
+    uint32_t j = perm[i];
+    f_out[(int64_t)comp * n + j] = F;
+    return;
+  }
+  if (p_out) p_out[(int64_t)comp * n + i] = ps[(int64_t)comp * n + i] + K * F;
+  if (f_out) f_out[(int64_t)comp * n + i] = F;
+  if (u_out) {
+    u_out[i] = ux;
+    u_out[n + i] = uy;
+    u_out[2 * n + i] = uz;
+    id_out[i] = ids[i];
+  }
+}
+
+// First half kick with the cached force, drift in fixed point, next sort key.
+__global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ p,
+                                  const float* __restrict__ f, int64_t n, float K1, float dscale,
+                                  int shift, int ntl, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ counts) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = i < n;
+  uint32_t key = 0xffffffffu;
+  if (ok) {
+    uint32_t uu[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float pv = p[d * n + i] + K1 * f[d * n + i];
+      p[d * n + i] = pv;
+      // u += rne(Delta p 2^32 / L), modulo 2^32
+      long long step = __float2ll_rn(dscale * pv);
+      uu[d] = u[d * n + i] + (uint32_t)(unsigned long long)step;
+      u[d * n + i] = uu[d];
+    }
+    key = tile_key(uu[0], uu[1], uu[2], shift, ntl);
+    keys[i] = key;
+  }
+  unsigned act = __ballot_sync(0xffffffffu, ok);
+  if (ok) {
+    unsigned peers = __match_any_sync(act, key);
+    int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(counts + key, (uint32_t)__popc(peers));
+  }
+}
+
+__global__ void k_repack_real(const float* __restrict__ src, int sp, float* __restrict__ dst,
+                              int dp, int nm) {
+  long long row = blockIdx.x;
+  for (int z = threadIdx.x; z < nm; z += blockDim.x) dst[row * dp + z] = src[row * sp + z];
+}
+
+__global__ void k_repack_complex(const float2* __restrict__ src, int sp, float2* __restrict__ dst,
+                                 int dp, int ncols) {
+  long long row = blockIdx.x;
+  for (int z = threadIdx.x; z < ncols; z += blockDim.x) dst[row * dp + z] = src[row * sp + z];
+}
+
+}  // namespace
+
+void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, int species,
+                 float* mesh, int row_pitch, cudaStream_t s) {
+  LaunchScope L(c, s, K_PAINT);
+  unsigned grid = (unsigned)(c->nt * c->nt * c->nt);
+  k_paint_tiles<<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species,
+                                               c->g.n, 32 - c->g.logn, c->ntl, row_pitch,
+                                               c->err_dev);
+}
+
+void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                  const float* mesh, int row_pitch, int comp, float K, float* p_out, float* f_out,
+                  uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter,
+                  cudaStream_t s) {
+  if (n == 0) return;
+  LaunchScope L(c, s, K_READOUT_KICK);
+  k_readout_kick<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      us, ps, ids, n, mesh, c->g.n, 32 - c->g.logn, row_pitch, comp, K, p_out, f_out, u_out,
+      id_out, perm_scatter);
+}
+
+void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,
+                     float dscale, cudaStream_t s) {
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (c->nbuckets + 1), s);
+  if (n == 0) return;
+  LaunchScope L(c, s, K_KICK_DRIFT_KEYS);
+  k_kick_drift_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0], c->counts);
+}
+
+void repack_real(pm_ctx* c, const Geom& g, const float* src, int sp, float* dst, int dp,
+                 cudaStream_t s) {
+  LaunchScope L(c, s, K_REPACK);
+  k_repack_real<<<(unsigned)g.rows(), 256, 0, s>>>(src, sp, dst, dp, g.n);
+}
+
+void repack_complex(pm_ctx* c, const Geom& g, const float2* src, int sp, float2* dst, int dp,
+                    cudaStream_t s) {
+  LaunchScope L(c, s, K_REPACK);
+  k_repack_complex<<<(unsigned)g.rows(), 256, 0, s>>>(src, sp, dst, dp, g.n / 2 + 1);
+}
+
+}  // namespace pmnu

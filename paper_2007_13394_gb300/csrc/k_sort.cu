@@ -1,0 +1,293 @@
+// Stable counting sort of particles into 16^3-cell tiles of the mesh.
+//
+// key = tile * 8 + face class (see pm.h, pm_sort).  The per-key counts (an
+// integer histogram, order independent) give every bucket's start by an
+// exclusive scan; the particle order inside the key space comes from a stable
+// least-significant-digit radix sort (8-bit digits) of (key, incoming index):
+// per pass, an upsweep histogram per 4096-key block, a scan of the
+// digit-major histogram, and a downsweep that ranks each key stably inside
+// its block (warp match + per-warp prefix, rounds in index order) and writes
+// it through shared memory so that global writes stay coalesced.
+#include <cuda_runtime.h>
+
+#include "pm_internal.cuh"
+
+namespace pmnu {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+
+constexpr int kRadixThreads = 256;
+constexpr int kRadixRounds = 16;
+constexpr int kRadixTile = kRadixThreads * kRadixRounds;  // 4096 keys per block
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+// ------------------------------------------------------------------ keys
+__global__ void k_keys(const uint32_t* __restrict__ u, int64_t n, int shift, int ntl,
+                       uint32_t* __restrict__ keys, uint32_t* __restrict__ counts) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = i < n;
+  uint32_t key = 0xffffffffu;
+  if (ok) {
+    key = tile_key(u[i], u[n + i], u[2 * n + i], shift, ntl);
+    keys[i] = key;
+  }
+  // warp-aggregated histogram increment
+  unsigned act = __ballot_sync(0xffffffffu, ok);
+  if (ok) {
+    unsigned peers = __match_any_sync(act, key);
+    int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(counts + key, (uint32_t)__popc(peers));
+  }
+}
+
+// ------------------------------------------------------------------ scan
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    uint32_t s = lane < nw ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) warp_sums[lane] = s;  // inclusive warp prefix
+  }
+  __syncthreads();
+  uint32_t before = (w > 0 ? warp_sums[w - 1] : 0u) + (x - v);
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const uint32_t* __restrict__ in,
+                                                            long long n,
+                                                            uint32_t* __restrict__ sums) {
+  __shared__ uint32_t ws[32];
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < n) s += in[base + k];
+  uint32_t tot;
+  block_exclusive_scan(s, ws, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __restrict__ in,
+                                                             long long n,
+                                                             const uint32_t* __restrict__ offs,
+                                                             uint32_t* __restrict__ out) {
+  __shared__ uint32_t ws[32];
+  long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  uint32_t run = block_exclusive_scan(s, ws, nullptr) + (offs ? offs[blockIdx.x] : 0u);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+}
+
+// ------------------------------------------------------------------ radix
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                              int64_t n, int shift,
+                                                              long long nblk,
+                                                              uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll 4
+  for (int r = 0; r < kRadixRounds; ++r) {
+    int64_t i = base + r * kRadixThreads + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(long long)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
+    long long nblk, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ hist_scan,
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+  __shared__ uint32_t sk[kRadixTile];
+  __shared__ uint32_t sv[kRadixTile];
+  __shared__ uint32_t wcnt[kRadixWarps][256];
+  __shared__ uint32_t running[256];
+  __shared__ uint32_t dstart[256];  // block-local start of each digit
+  __shared__ uint32_t gbase[256];   // global start of this block's run of each digit
+  __shared__ uint32_t ws[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+  {
+    uint32_t c = hist[(long long)t * nblk + blockIdx.x];
+    gbase[t] = hist_scan[(long long)t * nblk + blockIdx.x];
+    uint32_t ex = block_exclusive_scan(c, ws, nullptr);
+    dstart[t] = ex;
+    running[t] = 0;
+  }
+  __syncthreads();
+  for (int r = 0; r < kRadixRounds; ++r) {
+#pragma unroll
+    for (int q = 0; q < kRadixWarps; ++q) wcnt[q][t] = 0;
+    __syncthreads();
+    int64_t i = base + r * kRadixThreads + t;
+    bool ok = i < n;
+    uint32_t key = ok ? kin[i] : 0u;
+    uint32_t val = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
+    uint32_t d = ok ? ((key >> shift) & 255u) : (256u + lane);
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    int rank_w = __popc(peers & ((1u << lane) - 1u));
+    if (ok && rank_w == 0) wcnt[w][d] = __popc(peers);
+    __syncthreads();
+    {  // prefix over warps for digit t, on top of the earlier rounds
+      uint32_t acc = running[t];
+#pragma unroll
+      for (int q = 0; q < kRadixWarps; ++q) {
+        uint32_t c = wcnt[q][t];
+        wcnt[q][t] = acc;
+        acc += c;
+      }
+      running[t] = acc;
+    }
+    __syncthreads();
+    if (ok) {
+      uint32_t pos = dstart[d] + wcnt[w][d] + rank_w;
+      sk[pos] = key;
+      sv[pos] = val;
+    }
+    __syncthreads();
+  }
+  const int64_t cnt = (n - base) < kRadixTile ? (n - base) : kRadixTile;
+  for (int j = t; j < cnt; j += kRadixThreads) {
+    uint32_t key = sk[j];
+    uint32_t d = (key >> shift) & 255u;
+    uint32_t dst = gbase[d] + (j - dstart[d]);
+    kout[dst] = key;
+    vout[dst] = sv[j];
+  }
+}
+
+// ------------------------------------------------------------------ gather
+__global__ void k_gather(const uint32_t* __restrict__ u, const float* __restrict__ p,
+                         const uint32_t* __restrict__ id, int64_t n,
+                         const uint32_t* __restrict__ perm, uint32_t* __restrict__ us,
+                         float* __restrict__ ps, uint32_t* __restrict__ ids) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  uint32_t i = perm[k];
+  us[k] = u[i];
+  us[n + k] = u[n + i];
+  us[2 * n + k] = u[2 * n + i];
+  if (p) {
+    ps[k] = p[i];
+    ps[n + k] = p[n + i];
+    ps[2 * n + k] = p[2 * n + i];
+  }
+  ids[k] = id ? id[i] : i;
+}
+
+}  // namespace
+
+namespace {
+// Reduce-then-scan; level k keeps its block sums and their scanned offsets in tmp,
+// the next level works further along tmp (total < 2.001 * ceil(n / 4096) words).
+void scan_rec(pm_ctx* c, const uint32_t* in, uint32_t* out, long long n, uint32_t* tmp,
+              cudaStream_t s) {
+  long long nb = (n + kScanTile - 1) / kScanTile;
+  if (nb == 1) {
+    LaunchScope L(c, s, K_SCAN);
+    k_scan_apply<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+    return;
+  }
+  uint32_t* sums = tmp;
+  uint32_t* offs = tmp + nb;
+  {
+    LaunchScope L(c, s, K_SCAN);
+    k_scan_sums<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  }
+  scan_rec(c, sums, offs, nb, tmp + 2 * nb, s);
+  {
+    LaunchScope L(c, s, K_SCAN);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, offs, out);
+  }
+}
+}  // namespace
+
+void scan_exclusive(pm_ctx* c, const uint32_t* in, uint32_t* out, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  scan_rec(c, in, out, n, c->scan_tmp, s);
+}
+
+int build_keys(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
+  if (cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (c->nbuckets + 1), s) != cudaSuccess)
+    return PM_ECUDA;
+  if (n > 0) {
+    LaunchScope L(c, s, K_KEYS);
+    unsigned grid = (unsigned)((n + 255) / 256);
+    k_keys<<<grid, 256, 0, s>>>(u, n, 32 - c->g.logn, c->ntl, c->keys[0], c->counts);
+  }
+  return PM_OK;
+}
+
+int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
+  // bucket starts: exclusive scan of the nbuckets + 1 counts (last count is 0 -> total)
+  scan_exclusive(c, c->counts, c->bstart, c->nbuckets + 1, s);
+  if (n == 0) return PM_OK;
+  long long nblk = (n + kRadixTile - 1) / kRadixTile;
+  if (nblk > c->hist_blocks_max) return PM_EINVAL;
+  int cur = 0;
+  for (int pass = 0; pass < c->radix_passes; ++pass) {
+    int shift = 8 * pass;
+    {
+      LaunchScope L(c, s, K_RADIX_HIST);
+      k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
+    }
+    scan_exclusive(c, c->hist, c->hist_scan, 256 * nblk, s);
+    {
+      LaunchScope L(c, s, K_RADIX_SCATTER);
+      k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(
+          c->keys[cur], pass == 0 ? nullptr : c->vals[cur], n, shift, nblk, c->hist,
+          c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
+    }
+    cur ^= 1;
+  }
+  if (cur != 0) {  // keep the result in keys[0] / vals[0]
+    std::swap(c->keys[0], c->keys[1]);
+    std::swap(c->vals[0], c->vals[1]);
+  }
+  return PM_OK;
+}
+
+int sort_particles(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
+  int st = build_keys(c, u, n, s);
+  if (st != PM_OK) return st;
+  return radix_and_buckets(c, n, s);
+}
+
+void gather_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t* id, int64_t n,
+                   const uint32_t* perm, cudaStream_t s) {
+  if (n == 0) return;
+  LaunchScope L(c, s, K_GATHER);
+  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, p, id, n, perm, c->us, c->ps, c->ids);
+}
+
+}  // namespace pmnu

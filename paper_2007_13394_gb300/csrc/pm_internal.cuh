@@ -1,0 +1,208 @@
+// Internal context, launch bookkeeping and small device helpers of libpmnu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/pm.h"
+#include "cosmo.h"
+
+namespace pmnu {
+
+// Kernel kinds, for launch counting and per-kind CUDA-event timing.
+enum Kind {
+  K_KEYS = 0,
+  K_SCAN,
+  K_RADIX_HIST,
+  K_RADIX_SCATTER,
+  K_GATHER,
+  K_PAINT,
+  K_FFT_Z_R2C,
+  K_FFT_Y,
+  K_FFT_X_GREEN,
+  K_FFT_X_GRAD,
+  K_FFT_Z_C2R,
+  K_FFT_X_PLAIN,
+  K_READOUT_KICK,
+  K_KICK_DRIFT_KEYS,
+  K_POWER_BIN,
+  K_POWER_REDUCE,
+  K_IC_ZA,
+  K_IC_ASSEMBLE,
+  K_REPACK,
+  K_NUM_KINDS
+};
+
+constexpr int kTile = 16;        // tile edge in cells (the sort contract)
+constexpr int kMaxShell = 64;    // largest N_shell the mass table carries
+
+// Particle-mass lookup from the canonical id (passed by value to kernels).
+struct MassTable {
+  int64_t n_cdm;   // ids below are CDM
+  int64_t n_nu;    // neutrino ids follow
+  int32_t ndir;    // 2 nfib + 1
+  int32_t nshell;
+  float m_cdm;
+  float m_nu[kMaxShell];
+};
+
+// Mesh geometry for one FFT size.
+struct Geom {
+  int n = 0, logn = 0;   // points per side
+  int pc = 0;            // complex row pitch (float2) = n/2 + 2
+  long long rows() const { return (long long)n * n; }
+  size_t elems() const { return (size_t)n * n * pc; }  // float2 per padded mesh
+};
+
+struct Prof {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace pmnu
+
+struct pm_ctx {
+  int magic = 0;
+  int device = 0;
+  pm_config cfg{};
+  pmnu::Cosmo cosmo;
+  pmnu::Geom g;             // force mesh
+  int nt = 0, ntl = 0;      // tiles per side and its log2
+  long long nbuckets = 0;   // nt^3 * 8
+  int radix_passes = 0;
+  int64_t n_max = 0;
+  // meshes (two padded complex meshes, also viewed as padded real meshes)
+  float2* meshA = nullptr;
+  float2* meshB = nullptr;
+  // per-size tables: twiddles e^{-2 pi i t / n} (n entries), |k|^2, 1/sinc^4, k with Nyquist 0
+  std::map<int, float2*> tw;
+  float* ksq = nullptr;
+  float* winv = nullptr;
+  float* kvec0 = nullptr;
+  // sort / particle scratch
+  uint32_t* keys[2] = {nullptr, nullptr};
+  uint32_t* vals[2] = {nullptr, nullptr};
+  uint32_t* us = nullptr;
+  float* ps = nullptr;
+  uint32_t* ids = nullptr;
+  uint32_t* counts = nullptr;   // nbuckets + 1
+  uint32_t* bstart = nullptr;   // nbuckets + 1
+  uint32_t* hist = nullptr;     // 256 * radix blocks, raw
+  uint32_t* hist_scan = nullptr;
+  uint32_t* scan_tmp = nullptr;
+  size_t scan_tmp_elems = 0;
+  long long hist_blocks_max = 0;
+  // masses
+  pmnu::MassTable mt{};
+  double m_cdm = 0.0;
+  std::vector<double> m_nu, q_shell, m_shell, shell_edges;
+  // power binning partials
+  double* pk_partial = nullptr;
+  double* pk_final = nullptr;
+  // initial-condition tables
+  float* ic_amp = nullptr;      // sqrt(P/V) nc^1.5 by integer |n|^2, CDM and filtered neutrino
+  float* ic_amp_nu = nullptr;
+  long long ic_amp_len = 0;
+  double ic_kfs = -1.0;
+  // error word
+  int* err_dev = nullptr;
+  int* err_host = nullptr;
+  // host-array state used by pm_step_host
+  uint32_t* hs_u = nullptr;
+  float* hs_p = nullptr;
+  uint32_t* hs_id = nullptr;
+  float* hs_f = nullptr;
+  int64_t hs_cap = 0;
+  // instrumentation
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<pmnu::Prof> prof_live;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[pmnu::K_NUM_KINDS] = {};
+  int64_t prof_n[pmnu::K_NUM_KINDS] = {};
+};
+
+namespace pmnu {
+
+constexpr int kMagic = 0x504d4e55;
+
+// Launch bookkeeping: count, and when profiling, bracket with events on the stream.
+struct LaunchScope {
+  pm_ctx* c;
+  cudaStream_t s;
+  int kind;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LaunchScope(pm_ctx* ctx, cudaStream_t st, int k);
+  ~LaunchScope();
+};
+
+// host launch helpers implemented in the .cu files
+int sort_particles(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s);  // keys + radix -> vals
+int build_keys(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s);
+int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s);                 // after keys
+void scan_exclusive(pm_ctx* c, const uint32_t* in, uint32_t* out, long long n, cudaStream_t s);
+void gather_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t* id, int64_t n,
+                   const uint32_t* perm, cudaStream_t s);
+void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, int species,
+                 float* mesh, int row_pitch, cudaStream_t s);
+void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, cudaStream_t s);
+void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* buf, int comp,
+                           cudaStream_t s);
+void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
+void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                  const float* mesh, int row_pitch, int comp, float K, float* p_out, float* f_out,
+                  uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter,
+                  cudaStream_t s);
+void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,
+                     float dscale, cudaStream_t s);
+void repack_real(pm_ctx* c, const Geom& g, const float* src, int src_pitch, float* dst,
+                 int dst_pitch, cudaStream_t s);
+void repack_complex(pm_ctx* c, const Geom& g, const float2* src, int src_pitch, float2* dst,
+                    int dst_pitch, cudaStream_t s);
+int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* k_out,
+              double* P_out, int64_t* nmodes_out, cudaStream_t s);
+int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s);
+float2* twiddles(pm_ctx* c, int n);
+
+#define PM_CUDA_TRY(expr)                      \
+  do {                                         \
+    cudaError_t e_ = (expr);                   \
+    if (e_ != cudaSuccess) return PM_ECUDA;    \
+  } while (0)
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Sort key of a particle: tile of its cell (16^3 cells, x-major) * 8 + face class.
+__device__ __forceinline__ uint32_t tile_key(uint32_t ux, uint32_t uy, uint32_t uz, int shift,
+                                             int ntl) {
+  uint32_t cx = ux >> shift, cy = uy >> shift, cz = uz >> shift;
+  uint32_t tile = ((cx >> 4) << (2 * ntl)) | ((cy >> 4) << ntl) | (cz >> 4);
+  uint32_t cls = (((cx & 15u) == 15u) ? 4u : 0u) | (((cy & 15u) == 15u) ? 2u : 0u) |
+                 (((cz & 15u) == 15u) ? 1u : 0u);
+  return (tile << 3) | cls;
+}
+
+// Mass of a canonical id in units of the mean mass per cell; 0 if the species is masked.
+// Sets *bad for ids beyond the configured particle count.
+__device__ __forceinline__ float id_mass(const MassTable& mt, uint32_t id, int species, bool* bad) {
+  if ((int64_t)id < mt.n_cdm) return (species & PM_SPECIES_CDM) ? mt.m_cdm : 0.0f;
+  int64_t j = (int64_t)id - mt.n_cdm;
+  if (j >= mt.n_nu) {
+    *bad = true;
+    return 0.0f;
+  }
+  int shell = (int)((j / mt.ndir) % mt.nshell);
+  return (species & PM_SPECIES_NU) ? mt.m_nu[shell] : 0.0f;
+}
+
+}  // namespace pmnu

@@ -1,0 +1,348 @@
+"""Thin ctypes binding over libpmnu (include/pm.h).
+
+Argument marshalling only: every step of the particle-mesh path runs in the
+library's CUDA kernels.  Torch tensors supply device memory and the current
+stream; uint32 arrays (positions, ids, permutations) travel as int32 tensors
+with the same bits.  A missing or unloadable library raises ``RuntimeError``:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmnu.so")
+
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
+SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
+
+
+class PMError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__(f"{what}: {status} ({strerror(status)})")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double), ("nmesh", ctypes.c_int32), ("nc", ctypes.c_int32),
+        ("nsites", ctypes.c_int32), ("nshell", ctypes.c_int32), ("nfib", ctypes.c_int32),
+        ("h", ctypes.c_double), ("omega_m", ctypes.c_double), ("t_cmb", ctypes.c_double),
+        ("n_eff", ctypes.c_double), ("n_nu", ctypes.c_int32), ("pad0", ctypes.c_int32),
+        ("m_nu", ctypes.c_double * 3), ("a_ini_ode", ctypes.c_double), ("n_max", ctypes.c_int64),
+        ("ns", ctypes.c_double), ("sigma8", ctypes.c_double), ("flags", ctypes.c_uint32),
+        ("pad1", ctypes.c_int32),
+    ]
+
+
+class State(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_void_p), ("p", ctypes.c_void_p), ("id", ctypes.c_void_p), ("f", ctypes.c_void_p),
+        ("n", ctypes.c_int64), ("a", ctypes.c_double), ("f_valid", ctypes.c_int32), ("pad0", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpmnu.so (built by ``__graft_entry__.build()``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpmnu.so not found at {path}; run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, d = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sigs = {
+        "pm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "pm_cosmo_growth": (ctypes.c_int, [ctypes.POINTER(Config), d, dp]),
+        "pm_cosmo_coeffs": (ctypes.c_int, [ctypes.POINTER(Config), d, d, d, dp]),
+        "pm_cosmo_params": (ctypes.c_int, [ctypes.POINTER(Config), dp]),
+        "pm_nu_shells": (ctypes.c_int, [ctypes.POINTER(Config), dp, dp, dp]),
+        "pm_init": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(vp)]),
+        "pm_destroy": (ctypes.c_int, [vp]),
+        "pm_sync": (ctypes.c_int, [vp, vp]),
+        "pm_coeffs": (ctypes.c_int, [vp, d, d, d, dp]),
+        "pm_sort": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "pm_paint": (ctypes.c_int, [vp, vp, vp, i64, i32, vp, vp]),
+        "pm_force": (ctypes.c_int, [vp, vp, vp, i64, vp, vp]),
+        "pm_step": (ctypes.c_int, [vp, ctypes.POINTER(State), d, d, d, vp]),
+        "pm_step_host": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, ctypes.POINTER(i32), d, d, d, vp]),
+        "pm_power": (ctypes.c_int, [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
+        "pm_ic": (ctypes.c_int, [vp, vp, d, d, ctypes.POINTER(State), vp]),
+        "pm_fft_r2c": (ctypes.c_int, [vp, vp, vp, vp]),
+        "pm_fft_c2r": (ctypes.c_int, [vp, vp, vp, vp]),
+        "pm_potential": (ctypes.c_int, [vp, vp, vp, vp]),
+        "pm_force_mesh": (ctypes.c_int, [vp, vp, i32, vp, vp]),
+        "pm_readout": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "pm_launch_count": (i64, [vp]),
+        "pm_profile_enable": (ctypes.c_int, [vp, i32]),
+        "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
+        "pm_kernel_kinds": (i32, []),
+        "pm_kernel_name": (ctypes.c_char_p, [i32]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load_library().pm_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "?"
+
+
+def _check(status, what):
+    if status != PM_OK:
+        raise PMError(status, what)
+
+
+@dataclass
+class RunConfig:
+    """Python mirror of pm_config with the defaults of the synthetic workloads."""
+    box: float
+    nmesh: int
+    nc: int
+    nsites: int = 0
+    nshell: int = 10
+    nfib: int = 3
+    h: float = 0.68
+    omega_m: float = 0.31
+    t_cmb: float = 2.7255
+    n_eff: float = 3.046
+    m_nu: tuple = (0.0, 0.0, 0.0)
+    a_ini_ode: float = 1.0 / 160.0
+    n_max: int = 0
+    ns: float = 0.965
+    sigma8: float = 0.81
+    extra: dict = field(default_factory=dict)
+
+    def n_cdm(self) -> int:
+        return self.nc ** 3
+
+    def n_nu(self) -> int:
+        return self.nsites ** 3 * self.nshell * (2 * self.nfib + 1) if self.nsites else 0
+
+    def n_particles(self) -> int:
+        return self.n_cdm() + self.n_nu()
+
+    def to_c(self) -> Config:
+        c = Config()
+        c.box, c.nmesh, c.nc, c.nsites = self.box, self.nmesh, self.nc, self.nsites
+        c.nshell, c.nfib, c.h, c.omega_m = self.nshell, self.nfib, self.h, self.omega_m
+        c.t_cmb, c.n_eff = self.t_cmb, self.n_eff
+        m = [float(x) for x in self.m_nu]
+        c.n_nu = len(m)
+        for i, x in enumerate(m[:3]):
+            c.m_nu[i] = x
+        c.a_ini_ode = self.a_ini_ode
+        c.n_max = self.n_max or self.n_particles()
+        c.ns, c.sigma8 = self.ns, self.sigma8
+        return c
+
+
+# ----------------------------------------------------------------- host-only
+def cosmo_growth(cfg: RunConfig, a: float):
+    out = (ctypes.c_double * 4)()
+    _check(load_library().pm_cosmo_growth(ctypes.byref(cfg.to_c()), a, out), "pm_cosmo_growth")
+    return tuple(out)
+
+
+def cosmo_coeffs(cfg: RunConfig, a0: float, ah: float, a1: float):
+    out = (ctypes.c_double * 3)()
+    _check(load_library().pm_cosmo_coeffs(ctypes.byref(cfg.to_c()), a0, ah, a1, out), "pm_cosmo_coeffs")
+    return tuple(out)
+
+
+def cosmo_params(cfg: RunConfig):
+    out = (ctypes.c_double * 5)()
+    _check(load_library().pm_cosmo_params(ctypes.byref(cfg.to_c()), out), "pm_cosmo_params")
+    return dict(zip(["omega_gamma", "omega_c", "omega_nu", "omega_lambda", "kT_nu0"], out))
+
+
+def nu_shells(cfg: RunConfig):
+    e = (ctypes.c_double * (cfg.nshell + 1))()
+    q = (ctypes.c_double * cfg.nshell)()
+    m = (ctypes.c_double * cfg.nshell)()
+    _check(load_library().pm_nu_shells(ctypes.byref(cfg.to_c()), e, q, m), "pm_nu_shells")
+    return np.array(e), np.array(q), np.array(m)
+
+
+# ----------------------------------------------------------------- device
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required for the particle-mesh path")
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def as_u32_tensor(a: np.ndarray):
+    """Host uint32 array -> CUDA int32 tensor with the same bits."""
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def to_u32(t) -> np.ndarray:
+    return t.detach().cpu().numpy().view(np.uint32)
+
+
+class ParticleMesh:
+    """One library context (scratch meshes, sort buffers, FP64 growth tables)."""
+
+    def __init__(self, cfg: RunConfig):
+        self.cfg = cfg
+        self.lib = load_library()
+        _torch()
+        h = ctypes.c_void_p()
+        self._c = cfg.to_c()
+        _check(self.lib.pm_init(ctypes.byref(self._c), ctypes.byref(h)), "pm_init")
+        self.h = h
+        self.n = cfg.nmesh
+
+    def close(self):
+        if self.h:
+            self.lib.pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def sync(self):
+        _check(self.lib.pm_sync(self.h, _stream()), "pm_sync")
+
+    def coeffs(self, a0, ah, a1):
+        out = (ctypes.c_double * 5)()
+        _check(self.lib.pm_coeffs(self.h, a0, ah, a1, out), "pm_coeffs")
+        return tuple(out)
+
+    def sort(self, u):
+        torch = _torch()
+        n = u.shape[1]
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+        keys = torch.empty(n, dtype=torch.int32, device="cuda")
+        _check(self.lib.pm_sort(self.h, _ptr(u), n, _ptr(perm), _ptr(keys), _stream()), "pm_sort")
+        return perm, keys
+
+    def paint(self, u, ids=None, species=SPECIES_ALL):
+        torch = _torch()
+        mesh = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_paint(self.h, _ptr(u), _ptr(ids), u.shape[1], species, _ptr(mesh), _stream()),
+               "pm_paint")
+        return mesh
+
+    def force(self, u, ids=None):
+        torch = _torch()
+        n = u.shape[1]
+        F = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_force(self.h, _ptr(u), _ptr(ids), n, _ptr(F), _stream()), "pm_force")
+        return F
+
+    def step(self, st: dict, a0, ah, a1):
+        s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
+                  st["u"].shape[1], st.get("a", a0), int(st.get("f_valid", 0)), 0)
+        _check(self.lib.pm_step(self.h, ctypes.byref(s), a0, ah, a1, _stream()), "pm_step")
+        st["a"], st["f_valid"] = s.a, s.f_valid
+        return st
+
+    def step_host(self, u, p, ids, f, f_valid, a0, ah, a1, stream=None):
+        fv = ctypes.c_int32(int(f_valid))
+        rc = self.lib.pm_step_host(self.h, u.ctypes.data_as(ctypes.c_void_p), p.ctypes.data_as(ctypes.c_void_p),
+                                   ids.ctypes.data_as(ctypes.c_void_p), f.ctypes.data_as(ctypes.c_void_p),
+                                   u.shape[1], ctypes.byref(fv), a0, ah, a1,
+                                   stream if stream is not None else _stream())
+        _check(rc, "pm_step_host")
+        return fv.value
+
+    def new_state(self, n):
+        torch = _torch()
+        return {"u": torch.empty((3, n), dtype=torch.int32, device="cuda"),
+                "p": torch.empty((3, n), dtype=torch.float32, device="cuda"),
+                "id": torch.empty(n, dtype=torch.int32, device="cuda"),
+                "f": torch.zeros((3, n), dtype=torch.float32, device="cuda"),
+                "a": 0.0, "f_valid": 0}
+
+    def ic(self, noise, a0, k_fs=0.0):
+        """Zel'dovich ICs from device white noise (float32, nc^3)."""
+        st = self.new_state(self.cfg.n_particles())
+        s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
+                  st["u"].shape[1], a0, 0, 0)
+        _check(self.lib.pm_ic(self.h, _ptr(noise), a0, k_fs, ctypes.byref(s), _stream()), "pm_ic")
+        st["a"], st["f_valid"] = s.a, s.f_valid
+        return st
+
+    def power(self, u, ids=None, species_a=SPECIES_ALL, species_b=SPECIES_ALL, nbins=32):
+        k = np.zeros(nbins)
+        P = np.zeros(nbins)
+        nm = np.zeros(nbins, dtype=np.int64)
+        _check(self.lib.pm_power(self.h, _ptr(u), _ptr(ids), u.shape[1], species_a, species_b, nbins,
+                                 k.ctypes.data_as(ctypes.c_void_p), P.ctypes.data_as(ctypes.c_void_p),
+                                 nm.ctypes.data_as(ctypes.c_void_p), _stream()), "pm_power")
+        return k, P, nm
+
+    def fft_r2c(self, mesh):
+        torch = _torch()
+        out = torch.empty((self.n, self.n, self.n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_fft_r2c(self.h, _ptr(mesh), _ptr(out), _stream()), "pm_fft_r2c")
+        return out
+
+    def fft_c2r(self, cplx):
+        torch = _torch()
+        out = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_fft_c2r(self.h, _ptr(cplx), _ptr(out), _stream()), "pm_fft_c2r")
+        return out
+
+    def potential(self, mesh):
+        torch = _torch()
+        out = torch.empty((self.n, self.n, self.n // 2 + 1, 2), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_potential(self.h, _ptr(mesh), _ptr(out), _stream()), "pm_potential")
+        return out
+
+    def force_mesh(self, phi, comp):
+        torch = _torch()
+        out = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_force_mesh(self.h, _ptr(phi), comp, _ptr(out), _stream()), "pm_force_mesh")
+        return out
+
+    def readout(self, u, mesh):
+        torch = _torch()
+        out = torch.empty(u.shape[1], dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_readout(self.h, _ptr(u), u.shape[1], _ptr(mesh), _ptr(out), _stream()), "pm_readout")
+        return out
+
+    def launch_count(self):
+        return int(self.lib.pm_launch_count(self.h))
+
+    def profile(self, enable: bool):
+        _check(self.lib.pm_profile_enable(self.h, 1 if enable else 0), "pm_profile_enable")
+
+    def profile_read(self, reset=True):
+        out = {}
+        for k in range(self.lib.pm_kernel_kinds()):
+            ms = ctypes.c_double()
+            n = ctypes.c_int64()
+            _check(self.lib.pm_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0),
+                   "pm_profile_read")
+            if n.value:
+                out[self.lib.pm_kernel_name(k).decode()] = (ms.value, n.value)
+        return out
