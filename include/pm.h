@@ -220,8 +220,9 @@ int pm_readout(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* mesh, flo
 
 /* Number of kernels this context has launched since pm_init. */
 int64_t pm_launch_count(pm_ctx* ctx);
-/* Enable (1) or disable (0) CUDA-event timing of every launch, per kernel kind. */
-int pm_profile_enable(pm_ctx* ctx, int32_t enable);
+/* CUDA-event timing of launches on their own stream, per kernel kind: bit k of mask
+ * selects kind k (-1 = every kind, 0 = off). */
+int pm_profile_enable(pm_ctx* ctx, int32_t mask);
 /* Accumulated milliseconds and launches of kernel kind k (0 <= k < pm_kernel_kinds()),
  * synchronous; resets the kind's counters when reset != 0. */
 int pm_profile_read(pm_ctx* ctx, int32_t kind, double* ms, int64_t* launches, int32_t reset);

@@ -98,7 +98,7 @@ def displacement(dk, box, shift=0.0, k_fs=0.0):
     out = []
     for kj in (KX, KY, KZ):
         sk = 1j * kj * dk * inv * filt * phase
-        out.append(np.fft.irfftn(sk, s=(nc, nc, nc)))
+        out.append(np.fft.irfftn(sk, s=(nc, nc, nc), axes=(0, 1, 2)))
     return np.stack(out)
 
 

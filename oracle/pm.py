@@ -149,7 +149,7 @@ def force_mesh(phi_k, box, n, component):
     else:
         kj = np.where(nhalf == n // 2, 0.0, khalf)[None, None, :]
     fk = -1j * kj * phi_k
-    return np.fft.irfftn(fk, s=(n, n, n)) * n ** 3
+    return np.fft.irfftn(fk, s=(n, n, n), axes=(0, 1, 2)) * n ** 3
 
 
 def force(u, mass, n, box, omega_m0):

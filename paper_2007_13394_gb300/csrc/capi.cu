@@ -15,7 +15,7 @@ namespace pmnu {
 
 LaunchScope::LaunchScope(pm_ctx* ctx, cudaStream_t st, int k) : c(ctx), s(st), kind(k) {
   ++c->launches;
-  if (c->prof) {
+  if (c->prof & (1u << k)) {
     if (c->prof_pool.size() < 2) {
       cudaEvent_t a, b;
       cudaEventCreate(&a);
@@ -563,9 +563,9 @@ int pm_readout(pm_ctx* c, const uint32_t* u, int64_t n, const float* mesh, float
 
 int64_t pm_launch_count(pm_ctx* c) { return valid(c) ? c->launches : -1; }
 
-int pm_profile_enable(pm_ctx* c, int32_t enable) {
+int pm_profile_enable(pm_ctx* c, int32_t mask) {
   if (!valid(c)) return PM_ENOTINIT;
-  c->prof = enable != 0;
+  c->prof = (uint32_t)mask;
   return PM_OK;
 }
 

@@ -118,7 +118,7 @@ struct pm_ctx {
   int64_t hs_cap = 0;
   // instrumentation
   int64_t launches = 0;
-  bool prof = false;
+  uint32_t prof = 0;  // bit k: time kernel kind k
   std::vector<pmnu::Prof> prof_live;
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[pmnu::K_NUM_KINDS] = {};

@@ -333,8 +333,19 @@ class ParticleMesh:
     def launch_count(self):
         return int(self.lib.pm_launch_count(self.h))
 
-    def profile(self, enable: bool):
-        _check(self.lib.pm_profile_enable(self.h, 1 if enable else 0), "pm_profile_enable")
+    def kernel_kinds(self):
+        return [self.lib.pm_kernel_name(k).decode() for k in range(self.lib.pm_kernel_kinds())]
+
+    def profile(self, kinds=None):
+        """Time the named kernel kinds with CUDA events (None: all, []: off)."""
+        if kinds is None:
+            mask = -1
+        else:
+            names = self.kernel_kinds()
+            mask = 0
+            for k in kinds:
+                mask |= 1 << names.index(k)
+        _check(self.lib.pm_profile_enable(self.h, mask), "pm_profile_enable")
 
     def profile_read(self, reset=True):
         out = {}

@@ -1,0 +1,176 @@
+"""GPU vs oracle over whole runs: initial conditions, several KDK steps, P(k), the
+host-buffer entry point, and a sampled check at the benchmark's full size."""
+import numpy as np
+import pytest
+
+from oracle import background as obg
+from oracle import ic as oic
+from oracle import neutrinos as onu
+from oracle import pm as opm
+from paper_2007_13394_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def pm():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2007_13394_gb300 import pm as _pm
+    return _pm
+
+
+def _wrap(d):
+    return ((d.astype(np.int64) + 2 ** 31) % 2 ** 32) - 2 ** 31
+
+
+def oracle_ics(cfg, a0, seed, kfs):
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    noise = inputs.white_noise(cfg.nc, seed=seed)
+    plin = oic.linear_power(cfg.omega_m, cfg.h, cfg.ns, cfg.sigma8)
+    uc, pc = oic.cdm_particles(noise.astype(np.float64), cfg.box, plin, bg.D(a0), bg.gp(a0))
+    _, q, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+    un, pn = oic.neutrino_particles(noise.astype(np.float64), cfg.box, plin, bg.D(a0), bg.gp(a0), cfg.nsites,
+                                    cfg.nshell, cfg.nfib, q, onu.thermal_momentum_scale(bg.kT_nu0, max(cfg.m_nu)),
+                                    k_fs=kfs)
+    mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
+                                bg.omega_nu_poisson, m_shell)
+    mass = onu.particle_masses(uc.shape[1], un.shape[1], cfg.nshell, cfg.nfib, mc, mn)
+    return bg, noise, np.hstack([uc, un]), np.hstack([pc, pn]), mass, uc.shape[1]
+
+
+@pytest.mark.parametrize("kfs", [0.0, 0.05])
+def test_initial_conditions_match_oracle(pm, kfs):
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg1()
+    a0 = 0.01
+    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, a0, 1, kfs)
+    ctx = pm.ParticleMesh(cfg)
+    st = ctx.ic(torch.from_numpy(noise).cuda(), a0, k_fs=kfs)
+    ctx.sync()
+    assert np.array_equal(pm.to_u32(st["id"]), np.arange(u.shape[1], dtype=np.uint32))
+    du = _wrap(pm.to_u32(st["u"]).astype(np.int64) - u.astype(np.int64))
+    disp = _wrap(u.astype(np.int64) - pm.to_u32(st["u"]).astype(np.int64) * 0)   # scale reference
+    # positions agree to FP32 displacement rounding: < 1e-5 of a mesh cell
+    cell_quanta = 2 ** 32 / cfg.nmesh
+    assert np.abs(du).max() < 1e-5 * cell_quanta, np.abs(du).max()
+    pg = st["p"].cpu().numpy()
+    assert np.abs(pg - p).max() <= 1e-5 * np.abs(p).max()
+    del disp
+
+
+def test_ten_step_run_power_spectra_match_oracle(pm):
+    """cfg1 (256 Mpc/h, 32^3 + 8^3 x 70, mesh 64^3), 10 steps linear in a from z = 99 to 0:
+    P_cdm, P_m and P_cdm,nu within 0.1 % for k < k_Ny / 2."""
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg1()
+    a0 = 0.01
+    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, a0, 1, 0.0)
+    sched = obg.schedule_linear(0.01, 1.0, 10)
+    # oracle run
+    f = opm.force(u, mass, cfg.nmesh, cfg.box, bg.omega_m0)
+    uo, po = u.copy(), p.copy()
+    for (a, ah, b) in sched:
+        uo, po, f = opm.kdk_step(uo, po, f, obg.step_coefficients(bg, a, ah, b), mass, cfg.nmesh, cfg.box,
+                                 bg.omega_m0)
+    # GPU run from the same snapshot
+    ctx = pm.ParticleMesh(cfg)
+    st = ctx.new_state(u.shape[1])
+    st["u"].copy_(pm.as_u32_tensor(u))
+    st["p"].copy_(torch.from_numpy(p.astype(np.float32)))
+    st["id"].copy_(torch.arange(u.shape[1], dtype=torch.int32))
+    for (a, ah, b) in sched:
+        ctx.step(st, a, ah, b)
+    ctx.sync()
+    nb = 16
+    kny = np.pi * cfg.nmesh / cfg.box
+    sel_c = np.arange(u.shape[1]) < ncdm
+    meshes = {1: opm.paint(uo[:, sel_c], mass[sel_c], cfg.nmesh),
+              2: opm.paint(uo[:, ~sel_c], mass[~sel_c], cfg.nmesh),
+              3: opm.paint(uo, mass, cfg.nmesh)}
+    for (sa, sb) in ((1, 1), (3, 3), (1, 2)):
+        k, P, nm = ctx.power(st["u"], st["id"], species_a=sa, species_b=sb, nbins=nb)
+        ko, Po, no = opm.power_spectrum(meshes[sa], meshes[sb], cfg.box, nb)
+        sel = (no > 0) & (ko < kny / 2)
+        np.testing.assert_allclose(P[sel], Po[sel], rtol=1e-3, err_msg=f"P_{sa}{sb}")
+    ctx.sync()
+
+
+def test_step_host_equals_device_step(pm):
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg1()
+    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, 0.05, 3, 0.0)
+    ctx = pm.ParticleMesh(cfg)
+    st = ctx.new_state(u.shape[1])
+    st["u"].copy_(pm.as_u32_tensor(u))
+    st["p"].copy_(torch.from_numpy(p.astype(np.float32)))
+    st["id"].copy_(torch.arange(u.shape[1], dtype=torch.int32))
+    ctx.step(st, 0.05, 0.06, 0.07)
+    hu, hp = u.copy(), p.astype(np.float32)
+    hid = np.arange(u.shape[1], dtype=np.uint32)
+    hf = np.zeros_like(hp)
+    fv = ctx.step_host(hu, hp, hid, hf, 0, 0.05, 0.06, 0.07)
+    ctx.sync()
+    assert fv == 1
+    assert np.array_equal(hu, pm.to_u32(st["u"]))
+    assert np.array_equal(hp, st["p"].cpu().numpy())
+    assert np.array_equal(hid, pm.to_u32(st["id"]))
+
+
+def test_gpu_ic_then_steps_conserve_momentum(pm):
+    """The GPU-only path of the benchmark (ICs on the device, several steps): total momentum
+    stays at its initial value to FP32 accuracy, positions stay finite, ids stay a permutation."""
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg2_parity()
+    ctx = pm.ParticleMesh(cfg)
+    noise = torch.from_numpy(inputs.white_noise(cfg.nc, seed=2)).cuda()
+    st = ctx.ic(noise, 0.01, k_fs=workloads.free_streaming_k(cfg, 0.01))
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    _, _, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+    mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
+                                bg.omega_nu_poisson, m_shell)
+    table = onu.particle_masses(cfg.n_cdm(), cfg.n_nu(), cfg.nshell, cfg.nfib, mc, mn)
+    for (a, ah, b) in workloads.schedule_paper(25)[:6]:
+        ctx.step(st, a, ah, b)
+    ctx.sync()
+    ids = pm.to_u32(st["id"])
+    assert np.array_equal(np.sort(ids), np.arange(cfg.n_particles(), dtype=np.uint32))
+    f = st["f"].double().cpu().numpy()
+    m = table[ids]
+    net = np.abs((f * m).sum(axis=1)).max()
+    assert net < 1e-5 * np.abs(f * m).sum(axis=1).max()
+
+
+@pytest.mark.slow
+def test_full_size_benchmark_force_on_sampled_particles(pm):
+    """At the benchmark size (512^3 mesh, 256^3 + 32^3 x 70 particles), the GPU force at 4096
+    sampled particles against the oracle's FP64 mesh force read out at the same particles."""
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg2()
+    ctx = pm.ParticleMesh(cfg)
+    noise = torch.from_numpy(inputs.white_noise(cfg.nc, seed=1)).cuda()
+    st = ctx.ic(noise, 0.01, k_fs=workloads.free_streaming_k(cfg, 0.01))
+    for (a, ah, b) in workloads.schedule_paper(25)[:3]:
+        ctx.step(st, a, ah, b)
+    F = ctx.force(st["u"], st["id"])
+    ctx.sync()
+    u = pm.to_u32(st["u"])
+    ids = pm.to_u32(st["id"])
+    Fg = F.double().cpu().numpy()
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    _, _, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+    mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
+                                bg.omega_nu_poisson, m_shell)
+    mass = onu.particle_masses(cfg.n_cdm(), cfg.n_nu(), cfg.nshell, cfg.nfib, mc, mn)[ids]
+    phi = opm.potential_k(opm.paint(u, mass, cfg.nmesh), cfg.box, bg.omega_m0)
+    rng = np.random.default_rng(0)
+    pick = rng.choice(u.shape[1], 4096, replace=False)
+    ref = np.stack([opm.readout(u[:, pick], opm.force_mesh(phi, cfg.box, cfg.nmesh, j), cfg.nmesh)
+                    for j in range(3)])
+    got = Fg[:, pick]
+    rel = np.sqrt(((got - ref) ** 2).sum() / (ref ** 2).sum())
+    assert rel < 1e-5, rel

@@ -168,7 +168,7 @@ def test_fft_r2c_c2r_match_numpy(pm, n):
     assert err < 2e-6, err
     y = ctx.fft_c2r(torch.from_numpy(X).cuda()).cpu().numpy()
     ctx.sync()
-    yref = np.fft.irfftn(Xc, s=(n, n, n)) * n ** 3
+    yref = np.fft.irfftn(Xc, s=(n, n, n), axes=(0, 1, 2)) * n ** 3
     err2 = np.abs(y - yref).max() / np.abs(yref).max()
     assert err2 < 2e-6, err2
 
@@ -253,8 +253,11 @@ def test_step_matches_oracle(pm):
     f0 = opm.force(o["u"], o["mass"], cfg.nmesh, cfg.box, bg.omega_m0)
     u1, p1, f1 = opm.kdk_step(o["u"], o["p"], f0, obg.step_coefficients(bg, a0, ah, a1), o["mass"],
                               cfg.nmesh, cfg.box, bg.omega_m0)
-    du = ((u_gpu.astype(np.int64) - u1.astype(np.int64) + 2 ** 31) % 2 ** 32) - 2 ** 31
-    assert np.abs(du).max() <= 64          # quanta of L / 2^32: FP32 drift rounding
+    wrap = lambda d: ((d + 2 ** 31) % 2 ** 32) - 2 ** 31
+    du = wrap(u_gpu.astype(np.int64) - u1.astype(np.int64))
+    moved = wrap(u1.astype(np.int64) - o["u"].astype(np.int64))
+    # FP32 momenta and drift product: error relative to this step's displacement, in quanta
+    assert np.all(np.abs(du) <= 64 + 4e-6 * np.abs(moved)), np.abs(du).max()
     assert np.sqrt(((p_gpu - p1) ** 2).sum() / (p1 ** 2).sum()) < 1e-5
     assert np.sqrt(((f_gpu - f1) ** 2).sum() / (f1 ** 2).sum()) < 1e-5
     # the state is now in tile order: the sort of the stored positions is the identity
