@@ -216,6 +216,29 @@ int pm_force_mesh(pm_ctx* ctx, const float* phi_complex, int32_t component, floa
 int pm_readout(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* mesh, float* out,
                void* stream);
 
+/* ---- allocation-free variant --------------------------------------------------- */
+
+/* Binned power spectrum of two half-spectrum meshes, without allocating anything.
+ * (No counterpart in the paper: a library convenience.)  For callers that cannot
+ * call cudaMalloc where they need a spectrum: code running inside a memory pool or
+ * arena that owns the device's memory, graph-driven pipelines whose replays must
+ * not allocate, hosts that lent their free memory to another framework.  It needs
+ * no context (pm_init allocates) and uses, instead of context scratch, one
+ * file-scope device array of 3 MiB (256 x 3 x 512 doubles) that every GPU loading
+ * the library keeps until exit.
+ * delta_a, delta_b: device, N * N * (N/2 + 1) complex values as interleaved floats,
+ * kz fastest (the layout pm_fft_r2c writes); they may be the same array.  Each is
+ * divided by its own mean (its k = 0 mode over N^3).  Binning as pm_power.
+ * k_out, P_out, nmodes_out: device arrays of nbins doubles, written in stream order.
+ * Limits: nmesh a power of two in [32, 2048], 1 <= nbins <= 512, box > 0; anything
+ * else returns PM_EINVAL without touching the GPU.  The first call on a device
+ * resolves the array's device address (cudaGetSymbolAddress with that device
+ * current): make it before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race on it; nothing needs clearing between calls. */
+int pm_power_bin_noalloc(const float* delta_a, const float* delta_b, int32_t nmesh, double box,
+                         int32_t nbins, double* k_out, double* P_out, double* nmodes_out,
+                         void* stream);
+
 /* ---- instrumentation --------------------------------------------------------- */
 
 /* Number of kernels this context has launched since pm_init. */

@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_potential": (ctypes.c_int, [vp, vp, vp, vp]),
         "pm_force_mesh": (ctypes.c_int, [vp, vp, i32, vp, vp]),
         "pm_readout": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "pm_power_bin_noalloc": (ctypes.c_int, [vp, vp, i32, d, i32, vp, vp, vp, vp]),
         "pm_launch_count": (i64, [vp]),
         "pm_profile_enable": (ctypes.c_int, [vp, i32]),
         "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
@@ -179,6 +180,21 @@ def nu_shells(cfg: RunConfig):
 
 
 # ----------------------------------------------------------------- device
+def power_bin_noalloc(delta_a, delta_b, nmesh: int, box: float, nbins: int):
+    """Allocation-free binning of two half spectra (device tensors as pm_fft_r2c writes them).
+
+    Returns device tensors (k, P, n_modes) of float64; the library itself allocates
+    nothing (the output tensors are the caller's).
+    """
+    torch = _torch()
+    k = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    P = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    nm = torch.empty(nbins, dtype=torch.float64, device="cuda")
+    _check(load_library().pm_power_bin_noalloc(_ptr(delta_a), _ptr(delta_b), nmesh, box, nbins, _ptr(k), _ptr(P),
+                                               _ptr(nm), _stream()), "pm_power_bin_noalloc")
+    return k, P, nm
+
+
 def _torch():
     import torch
     if not torch.cuda.is_available():
