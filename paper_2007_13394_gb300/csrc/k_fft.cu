@@ -161,7 +161,7 @@ constexpr int kZThreads = 256;
 
 // z pass, real -> complex, in place on rows of pitch P float2.
 template <int LOGN>
-__global__ void __launch_bounds__(kZThreads) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
+__global__ void __launch_bounds__(kZThreads, 4) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
                                                          int pc, const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
   constexpr int LS = M + M / 16 + 2;  // line stride in shared memory
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kZThreads) k_fft_z_r2c(float2* __restrict__ da
 
 // z pass, complex -> real, in place.
 template <int LOGN>
-__global__ void __launch_bounds__(kZThreads) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
+__global__ void __launch_bounds__(kZThreads, 4) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
                                                          int pc, const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
   constexpr int LS = M + M / 16 + 2;
@@ -202,7 +202,12 @@ __global__ void __launch_bounds__(kZThreads) k_fft_z_c2r(float2* __restrict__ da
   const bool ok = row < nrows;
   float2* rp = data + row * pc;
   float2* ls = sm + line * LS;
-  for (int k = j; k <= M; k += TPL) ls[padi(k)] = ok ? rp[k] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int k = j + s * TPL;
+    ls[padi(k)] = ok ? rp[k] : make_float2(0.f, 0.f);
+  }
+  if (j == 0) ls[padi(M)] = ok ? rp[M] : make_float2(0.f, 0.f);
   __syncthreads();
   float2 v[16];
 #pragma unroll
@@ -235,8 +240,9 @@ enum { EPI_NONE = 0, EPI_GREEN = 1 };
 enum { PRO_NONE = 0, PRO_GRAD = 1 };
 
 // Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK).
+// 64 registers a thread: two 512-thread CTAs (or four of 256) resident per SM
 template <int LOGM, int TK, bool INV, int EPI, int PRO>
-__global__ void __launch_bounds__(TK*(1 << LOGM) / 16) k_fft_strided(
+__global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) / 16)) k_fft_strided(
     const float2* __restrict__ src, float2* __restrict__ dst, int axis, int pc, int ntiles_z,
     const float2* __restrict__ tw, KTables kt, int comp) {
   constexpr int M = 1 << LOGM, Q = M / 16;
