@@ -111,6 +111,9 @@ def algorithmic_bytes(kind, n_mesh, n_particles):
         "paint_tiles": 16 * n_particles + 4 * cells,           # u + id read, mesh written once
         # u 12 + p_j 4 read, p_j 4 + f_j 4 written, mesh read once; u, id copy-back on 1 of 3
         "readout_kick": 24 * n_particles + 4 * cells + (12 + 4 + 4 + 8) * n_particles // 3,
+        "fft_x_fused": 4 * half,                                # read once, three components written
+        # u, p, id read; p, f, u, id written (tile order); three meshes read once
+        "readout3_kick": 68 * n_particles + 12 * cells,
         "kick_drift_keys": 64 * n_particles,
         "gather": 64 * n_particles,
         "radix_scatter": 16 * n_particles,

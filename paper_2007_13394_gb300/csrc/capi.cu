@@ -83,6 +83,7 @@ int dalloc(T** p, size_t count) {
 void free_all(pm_ctx* c) {
   cudaFree(c->meshA);
   cudaFree(c->meshB);
+  cudaFree(c->meshC);
   for (auto& kv : c->tw) cudaFree(kv.second);
   cudaFree(c->ksq);
   cudaFree(c->winv);
@@ -122,12 +123,19 @@ int sort_into_scratch(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
   return sort_particles(c, u, n, s);
 }
 
-// Paint of the sorted scratch particles into meshA (padded), then force component
-// meshes one at a time.  Callback per component with the real padded mesh in meshA.
-template <class F>
-int force_components(pm_ctx* c, int64_t n, cudaStream_t s, F&& per_comp) {
+// Paint of the sorted scratch particles into meshA (padded), then the force at every
+// sorted particle.  With the third mesh: the fused x pass gives all three component
+// meshes and one readout reads them (per_all); without it, one component mesh at a
+// time in meshA (per_comp).
+template <class F1, class F3>
+int force_components(pm_ctx* c, int64_t n, cudaStream_t s, F1&& per_comp, F3&& per_all) {
   float* realA = reinterpret_cast<float*>(c->meshA);
   paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, 2 * c->g.pc, s);
+  if (c->meshC) {
+    fft_force_fused(c, c->g, c->meshA, c->meshB, c->meshC, s);
+    per_all(realA, reinterpret_cast<float*>(c->meshB), reinterpret_cast<float*>(c->meshC));
+    return PM_OK;
+  }
   fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
   for (int comp = 0; comp < 3; ++comp) {
     fft_inverse_component(c, c->g, c->meshB, c->meshA, comp, s);
@@ -157,10 +165,16 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
     rc = sort_into_scratch(c, st->u, n, s);
     if (rc != PM_OK) return rc;
     gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
-    force_components(c, n, s, [&](int comp, float* mesh) {
-      readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, st->p, st->f,
-                   comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
-    });
+    force_components(
+        c, n, s,
+        [&](int comp, float* mesh) {
+          readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, st->p, st->f,
+                       comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
+        },
+        [&](float* mx, float* my, float* mz) {
+          readout3_kick(c, c->us, c->ps, c->ids, n, mx, my, mz, 2 * c->g.pc, 0.0f, st->p, st->f,
+                        st->u, st->id, nullptr, s);
+        });
     st->f_valid = 1;
   }
   // first half kick + drift + keys of the drifted positions
@@ -169,10 +183,16 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
   if (rc != PM_OK) return rc;
   gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
   // force at a1 and the second half kick, written back in tile order
-  force_components(c, n, s, [&](int comp, float* mesh) {
-    readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, (float)k[2], st->p, st->f,
-                 comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
-  });
+  force_components(
+      c, n, s,
+      [&](int comp, float* mesh) {
+        readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, (float)k[2], st->p, st->f,
+                     comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
+      },
+      [&](float* mx, float* my, float* mz) {
+        readout3_kick(c, c->us, c->ps, c->ids, n, mx, my, mz, 2 * c->g.pc, (float)k[2], st->p,
+                      st->f, st->u, st->id, nullptr, s);
+      });
   st->a = a1;
   st->f_valid = 1;
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
@@ -265,7 +285,9 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
   c->nbuckets = (long long)c->nt * c->nt * c->nt * 8;
   int bits = 0;
   while ((1LL << bits) < c->nbuckets) ++bits;
-  c->radix_passes = std::max(1, (bits + 7) / 8);
+  // 18-bit keys or fewer: two 9-bit passes; else 8-bit passes
+  c->radix_bits = bits <= 18 ? 9 : 8;
+  c->radix_passes = std::max(1, (bits + c->radix_bits - 1) / c->radix_bits);
   c->n_max = cfg->n_max;
   if (c->n_max >= (int64_t)0xffffffffLL) {
     delete c;
@@ -304,18 +326,20 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
   const int64_t nm = std::max<int64_t>(c->n_max, 1);
   const long long hb = (nm + 4095) / 4096;
   c->hist_blocks_max = hb;
-  const long long scan_n = std::max<long long>(256 * hb, c->nbuckets + 1);
+  const long long scan_n = std::max<long long>(512 * hb, c->nbuckets + 1);
   {  // every level of the recursive scan keeps 2 * blocks words
     size_t need = 64;
     for (long long m = scan_n; m > 1; m = (m + 4095) / 4096) need += 2 * (size_t)((m + 4095) / 4096);
     c->scan_tmp_elems = need;
   }
-  if (dalloc(&c->meshA, me) || dalloc(&c->meshB, me) || dalloc(&c->ksq, N) ||
+  const bool two_mesh = (cfg->flags & 1u) != 0;  // flag bit 0: per-component force path
+  if ((!two_mesh && dalloc(&c->meshC, me)) || dalloc(&c->meshA, me) || dalloc(&c->meshB, me) ||
+      dalloc(&c->ksq, N) ||
       dalloc(&c->winv, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
       dalloc(&c->keys[1], nm) || dalloc(&c->vals[0], nm) || dalloc(&c->vals[1], nm) ||
       dalloc(&c->us, 3 * nm) || dalloc(&c->ps, 3 * nm) || dalloc(&c->ids, nm) ||
       dalloc(&c->counts, c->nbuckets + 1) || dalloc(&c->bstart, c->nbuckets + 1) ||
-      dalloc(&c->hist, 256 * hb) || dalloc(&c->hist_scan, 256 * hb) ||
+      dalloc(&c->hist, 512 * hb) || dalloc(&c->hist_scan, 512 * hb) ||
       dalloc(&c->scan_tmp, c->scan_tmp_elems) || dalloc(&c->pk_partial, (size_t)N * 3 * 2048) ||
       dalloc(&c->pk_final, 3 * 2048) || dalloc(&c->err_dev, 1)) {
     free_all(c);
@@ -429,10 +453,16 @@ int pm_force(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, float*
   int rc = sort_into_scratch(c, u, n, s);
   if (rc != PM_OK) return rc;
   gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
-  force_components(c, n, s, [&](int comp, float* mesh) {
-    readout_kick(c, c->us, nullptr, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, nullptr, F_out,
-                 nullptr, nullptr, c->vals[0], s);
-  });
+  force_components(
+      c, n, s,
+      [&](int comp, float* mesh) {
+        readout_kick(c, c->us, nullptr, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, nullptr, F_out,
+                     nullptr, nullptr, c->vals[0], s);
+      },
+      [&](float* mx, float* my, float* mz) {
+        readout3_kick(c, c->us, nullptr, c->ids, n, mx, my, mz, 2 * c->g.pc, 0.0f, nullptr, F_out,
+                      nullptr, nullptr, c->vals[0], s);
+      });
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
 
@@ -589,7 +619,8 @@ const char* pm_kernel_name(int32_t k) {
       "keys",          "scan",         "radix_hist",   "radix_scatter",   "gather",
       "paint_tiles",   "fft_z_r2c",    "fft_y",        "fft_x_green",     "fft_x_grad",
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
-      "power_reduce",  "ic_za",        "ic_assemble",  "repack"};
+      "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
+      "readout3_kick"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

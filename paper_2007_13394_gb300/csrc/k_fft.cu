@@ -284,6 +284,83 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
   for (int s = 0; s < 16; ++s) dst[base + (long long)(j + s * Q) * stride] = v[s];
 }
 
+// Fused x pass of the force: forward x FFT of one column tile, Green's function,
+// then the three force components.  k_y and k_z are constant along an x line, so
+// IFFT_x(-i k_y phi) = -i k_y IFFT_x(phi) (same for z): two inverse transforms give
+// all three components.  Writes component x in place over the input, y and z to
+// two further meshes.  phi is parked in shared memory between the inverses.
+template <int LOGM, int TK>
+__global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) / 16)) k_fft_x_fused(
+    float2* __restrict__ a, float2* __restrict__ b, float2* __restrict__ cz, int pc, int ntiles_z,
+    const float2* __restrict__ tw, KTables kt) {
+  constexpr int M = 1 << LOGM, Q = M / 16;
+  extern __shared__ float2 sm[];
+  float2* work = sm;
+  float2* phis = sm + (M + M / 16 + 1) * TK;
+  const int c = threadIdx.x % TK, j = threadIdx.x / TK;
+  const int outer = blockIdx.x / ntiles_z;                  // ky index
+  const int kz = (blockIdx.x % ntiles_z) * TK + c;
+  const bool ok = kz <= M / 2;
+  const long long stride = (long long)M * pc;
+  const long long base = (long long)outer * pc + kz;
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s)
+    v[s] = ok ? a[base + (long long)(j + s * Q) * stride] : make_float2(0.f, 0.f);
+  run_stages<M, M, 1, false>(v, j, work + c, TK, tw);
+  {
+    const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
+    const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int kx = j + s * Q;
+      const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
+      float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
+      if (k2 == 0.0f) g = 0.0f;
+      v[s] = cscale(v[s], g);
+      phis[(j + s * Q) * TK + c] = v[s];                   // read back by this thread only
+      const float kk = __ldg(kt.kvec0 + kx);
+      v[s] = make_float2(kk * v[s].y, -kk * v[s].x);       // -i k_x phi
+    }
+  }
+  run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) a[base + (long long)(j + s * Q) * stride] = v[s];
+  }
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = phis[(j + s * Q) * TK + c];
+  run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
+  if (!ok) return;
+  const float ky0 = __ldg(kt.kvec0 + outer), kz0 = __ldg(kt.kvec0 + kz);
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const long long idx = base + (long long)(j + s * Q) * stride;
+    b[idx] = make_float2(ky0 * v[s].y, -ky0 * v[s].x);
+    cz[idx] = make_float2(kz0 * v[s].y, -kz0 * v[s].x);
+  }
+}
+
+template <int LOGM>
+constexpr int tk_fused() {
+  return LOGM >= 10 ? 4 : (LOGM == 9 ? 8 : 16);
+}
+
+template <int LOGM>
+void launch_x_fused(float2* a, float2* b, float2* cz, int pc, const float2* tw, const KTables& kt,
+                    cudaStream_t s) {
+  constexpr int M = 1 << LOGM, TK = tk_fused<LOGM>();
+  constexpr int threads = TK * M / 16;
+  const int ntz = (M / 2 + 1 + TK - 1) / TK;
+  const size_t smem = sizeof(float2) * ((size_t)(M + M / 16 + 1) * TK + (size_t)M * TK);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_fft_x_fused<LOGM, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_fft_x_fused<LOGM, TK><<<(unsigned)(M * ntz), threads, smem, s>>>(a, b, cz, pc, ntz, tw, kt);
+}
+
 template <int LOGM>
 constexpr int tk_for() {
   return LOGM >= 11 ? 4 : (LOGM == 10 ? 8 : 16);
@@ -403,6 +480,43 @@ void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* 
   {
     LaunchScope L(c, s, K_FFT_Z_C2R);
     dispatch_z(g, buf, tw, true, s);
+  }
+}
+
+void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz, cudaStream_t s) {
+  const float2* tw = twiddles(c, g.n);
+  KTables kt = ktables(c, g);
+  {
+    LaunchScope L(c, s, K_FFT_Z_R2C);
+    dispatch_z(g, a, tw, false, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, a, a, 1, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_X_FUSED);
+    switch (g.logn) {
+      case 5: launch_x_fused<5>(a, b, cz, g.pc, tw, kt, s); break;
+      case 6: launch_x_fused<6>(a, b, cz, g.pc, tw, kt, s); break;
+      case 7: launch_x_fused<7>(a, b, cz, g.pc, tw, kt, s); break;
+      case 8: launch_x_fused<8>(a, b, cz, g.pc, tw, kt, s); break;
+      case 9: launch_x_fused<9>(a, b, cz, g.pc, tw, kt, s); break;
+      case 10: launch_x_fused<10>(a, b, cz, g.pc, tw, kt, s); break;
+      case 11: launch_x_fused<11>(a, b, cz, g.pc, tw, kt, s); break;
+      default: break;
+    }
+  }
+  float2* bufs[3] = {a, b, cz};
+  for (int comp = 0; comp < 3; ++comp) {
+    {
+      LaunchScope L(c, s, K_FFT_Y);
+      dispatch_strided<true, EPI_NONE, PRO_NONE>(g, bufs[comp], bufs[comp], 1, tw, kt, 0, s);
+    }
+    {
+      LaunchScope L(c, s, K_FFT_Z_C2R);
+      dispatch_z(g, bufs[comp], tw, true, s);
+    }
   }
 }
 

@@ -59,42 +59,59 @@ __device__ __forceinline__ void paint_one(long long* acc, uint32_t ux, uint32_t 
   }
 }
 
+// The 14 bucket runs a tile reads, as (neighbour offset o, first class, end class):
+// its own tile (all classes), then for each low-side neighbour o the classes that
+// contain every bit of o, merged where they are contiguous.
+__constant__ int8_t c_runs[14][3] = {{0, 0, 8}, {4, 4, 8}, {2, 2, 4}, {2, 6, 8}, {1, 1, 2},
+                                     {1, 3, 4}, {1, 5, 6}, {1, 7, 8}, {6, 6, 8}, {5, 5, 6},
+                                     {5, 7, 8}, {3, 3, 4}, {3, 7, 8}, {7, 7, 8}};
+
 __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
     int nm, int shift, int ntl, int row_pitch, int* __restrict__ err) {
   __shared__ long long acc[kTileCells];
+  __shared__ uint32_t run_lo[14], run_pre[15];
   const int t = threadIdx.x;
   for (int i = t; i < kTileCells; i += kPaintThreads) acc[i] = 0;
-  __syncthreads();
   const int nt = 1 << ntl;
   const uint32_t tile = blockIdx.x;
   const int tx = tile >> (2 * ntl), ty = (tile >> ntl) & (nt - 1), tz = tile & (nt - 1);
+  if (t < 32) {  // one warp resolves the 14 runs and their prefix
+    uint32_t lo = 0, len = 0;
+    if (t < 14) {
+      const int o = c_runs[t][0];
+      const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
+      const uint32_t nb = ((uint32_t)((tx - ox) & (nt - 1)) << (2 * ntl)) |
+                          ((uint32_t)((ty - oy) & (nt - 1)) << ntl) | (uint32_t)((tz - oz) & (nt - 1));
+      lo = bstart[nb * 8 + c_runs[t][1]];
+      len = bstart[nb * 8 + c_runs[t][2]] - lo;
+    }
+    uint32_t x = len;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (t >= d) x += y;
+    }
+    if (t < 14) {
+      run_lo[t] = lo;
+      run_pre[t + 1] = x;
+    }
+    if (t == 0) run_pre[0] = 0;
+  }
+  __syncthreads();
   const float fscale = 1.0f / (float)(1u << shift);
   const uint32_t fmask = (1u << shift) - 1u;
+  const uint32_t total = run_pre[14];
   bool bad = false;
-  // o = 0: own tile (all classes); o = 1..7: low-side neighbour along the set bits,
-  // classes that contain every bit of o
-  for (int o = 0; o < 8; ++o) {
-    const int ox = (o >> 2) & 1, oy = (o >> 1) & 1, oz = o & 1;
-    const uint32_t nb = ((uint32_t)((tx - ox) & (nt - 1)) << (2 * ntl)) |
-                        ((uint32_t)((ty - oy) & (nt - 1)) << ntl) | (uint32_t)((tz - oz) & (nt - 1));
-    for (int cls = 0; cls < 8; ++cls) {
-      if ((cls & o) != o) continue;
-      uint32_t lo = bstart[nb * 8 + cls], hi;
-      if (o == 0) {  // own tile: one contiguous run over all classes
-        hi = bstart[nb * 8 + 8];
-        cls = 8;
-      } else {
-        hi = bstart[nb * 8 + cls + 1];
-      }
-      for (uint32_t k = lo + t; k < hi; k += kPaintThreads) {
-        float m = id_mass(mt, ids[k], species, &bad);
-        if (m == 0.0f) continue;
-        paint_one(acc, us[k], us[n + k], us[2 * n + k], m, shift, nm, tx * kTile, ty * kTile,
-                  tz * kTile, fscale, fmask);
-      }
-    }
+  int r = 0;
+  for (uint32_t v = t; v < total; v += kPaintThreads) {
+    while (v >= run_pre[r + 1]) ++r;   // v only grows, so the run index only grows
+    const uint32_t k = run_lo[r] + (v - run_pre[r]);
+    float m = id_mass(mt, ids[k], species, &bad);
+    if (m == 0.0f) continue;
+    paint_one(acc, us[k], us[n + k], us[2 * n + k], m, shift, nm, tx * kTile, ty * kTile,
+              tz * kTile, fscale, fmask);
   }
   if (bad) atomicOr(err, 1);
   __syncthreads();
@@ -143,6 +160,56 @@ __global__ void k_readout_kick(const uint32_t* __restrict__ us, const float* __r
   }
   if (p_out) p_out[(int64_t)comp * n + i] = ps[(int64_t)comp * n + i] + K * F;
   if (f_out) f_out[(int64_t)comp * n + i] = F;
+  if (u_out) {
+    u_out[i] = ux;
+    u_out[n + i] = uy;
+    u_out[2 * n + i] = uz;
+    id_out[i] = ids[i];
+  }
+}
+
+// CIC readout of all three force meshes at once, fused with the kick p += K F.
+__global__ void k_readout3_kick(const uint32_t* __restrict__ us, const float* __restrict__ ps,
+                                const uint32_t* __restrict__ ids, int64_t n,
+                                const float* __restrict__ mx, const float* __restrict__ my,
+                                const float* __restrict__ mz, int nm, int shift, int row_pitch,
+                                float K, float* __restrict__ p_out, float* __restrict__ f_out,
+                                uint32_t* __restrict__ u_out, uint32_t* __restrict__ id_out,
+                                const uint32_t* __restrict__ perm) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t ux = us[i], uy = us[n + i], uz = us[2 * n + i];
+  const float fscale = 1.0f / (float)(1u << shift);
+  const uint32_t fmask = (1u << shift) - 1u;
+  const int cx = ux >> shift, cy = uy >> shift, cz = uz >> shift;
+  const int cx1 = (cx + 1) & (nm - 1), cy1 = (cy + 1) & (nm - 1), cz1 = (cz + 1) & (nm - 1);
+  const float fx = (float)(ux & fmask) * fscale, fy = (float)(uy & fmask) * fscale,
+              fz = (float)(uz & fmask) * fscale;
+  const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+  const size_t r00 = ((size_t)cx * nm + cy) * row_pitch, r01 = ((size_t)cx * nm + cy1) * row_pitch;
+  const size_t r10 = ((size_t)cx1 * nm + cy) * row_pitch, r11 = ((size_t)cx1 * nm + cy1) * row_pitch;
+  const float w000 = gx * gy * gz, w001 = gx * gy * fz, w010 = gx * fy * gz, w011 = gx * fy * fz;
+  const float w100 = fx * gy * gz, w101 = fx * gy * fz, w110 = fx * fy * gz, w111 = fx * fy * fz;
+  const float* m[3] = {mx, my, mz};
+  float F[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float* g = m[d];
+    F[d] = w000 * __ldg(g + r00 + cz) + w001 * __ldg(g + r00 + cz1) + w010 * __ldg(g + r01 + cz) +
+           w011 * __ldg(g + r01 + cz1) + w100 * __ldg(g + r10 + cz) + w101 * __ldg(g + r10 + cz1) +
+           w110 * __ldg(g + r11 + cz) + w111 * __ldg(g + r11 + cz1);
+  }
+  if (perm) {  // force in the caller's order
+    const uint32_t j = perm[i];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) f_out[(int64_t)d * n + j] = F[d];
+    return;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (p_out) p_out[(int64_t)d * n + i] = ps[(int64_t)d * n + i] + K * F[d];
+    if (f_out) f_out[(int64_t)d * n + i] = F[d];
+  }
   if (u_out) {
     u_out[i] = ux;
     u_out[n + i] = uy;
@@ -213,6 +280,17 @@ void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t
   k_readout_kick<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
       us, ps, ids, n, mesh, c->g.n, 32 - c->g.logn, row_pitch, comp, K, p_out, f_out, u_out,
       id_out, perm_scatter);
+}
+
+void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                   const float* mx, const float* my, const float* mz, int row_pitch, float K,
+                   float* p_out, float* f_out, uint32_t* u_out, uint32_t* id_out,
+                   const uint32_t* perm_scatter, cudaStream_t s) {
+  if (n == 0) return;
+  LaunchScope L(c, s, K_READOUT3_KICK);
+  k_readout3_kick<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      us, ps, ids, n, mx, my, mz, c->g.n, 32 - c->g.logn, row_pitch, K, p_out, f_out, u_out, id_out,
+      perm_scatter);
 }
 
 void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,

@@ -3,7 +3,8 @@
 // key = tile * 8 + face class (see pm.h, pm_sort).  The per-key counts (an
 // integer histogram, order independent) give every bucket's start by an
 // exclusive scan; the particle order inside the key space comes from a stable
-// least-significant-digit radix sort (8-bit digits) of (key, incoming index):
+// least-significant-digit radix sort of (key, incoming index) with 8- or 9-bit
+// digits (two 9-bit passes cover the 18-bit keys of meshes up to 512^3):
 // per pass, an upsweep histogram per 4096-key block, a scan of the
 // digit-major histogram, and a downsweep that ranks each key stably inside
 // its block (warp match + per-warp prefix, rounds in index order) and writes
@@ -107,66 +108,93 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* __r
 }
 
 // ------------------------------------------------------------------ radix
+// Digit width BITS (8 or 9): DIG digits, each of the 256 threads owns DIG / 256 of them.
+template <int BITS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __restrict__ keys,
                                                               int64_t n, int shift,
                                                               long long nblk,
                                                               uint32_t* __restrict__ hist) {
-  __shared__ uint32_t cnt[256];
-  cnt[threadIdx.x] = 0;
+  constexpr int DIG = 1 << BITS, PER = DIG / kRadixThreads;
+  constexpr uint32_t MASK = DIG - 1;
+  __shared__ uint32_t cnt[DIG];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) cnt[threadIdx.x + q * kRadixThreads] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * kRadixTile;
 #pragma unroll 4
   for (int r = 0; r < kRadixRounds; ++r) {
     int64_t i = base + r * kRadixThreads + threadIdx.x;
-    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & MASK], 1u);
   }
   __syncthreads();
-  hist[(long long)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int d = threadIdx.x + q * kRadixThreads;
+    hist[(long long)d * nblk + blockIdx.x] = cnt[d];
+  }
 }
 
+template <int BITS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
     long long nblk, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ hist_scan,
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
-  __shared__ uint32_t sk[kRadixTile];
-  __shared__ uint32_t sv[kRadixTile];
-  __shared__ uint32_t wcnt[kRadixWarps][256];
-  __shared__ uint32_t running[256];
-  __shared__ uint32_t dstart[256];  // block-local start of each digit
-  __shared__ uint32_t gbase[256];   // global start of this block's run of each digit
+  constexpr int DIG = 1 << BITS, PER = DIG / kRadixThreads;
+  constexpr uint32_t MASK = DIG - 1;
+  extern __shared__ uint32_t stage_kv[];  // keys then values of the block, in digit order
+  uint32_t* sk = stage_kv;
+  uint32_t* sv = stage_kv + kRadixTile;
+  __shared__ uint32_t wcnt[kRadixWarps][DIG];
+  __shared__ uint32_t running[DIG];
+  __shared__ uint32_t dstart[DIG];  // block-local start of each digit
+  __shared__ uint32_t gbase[DIG];   // global start of this block's run of each digit
   __shared__ uint32_t ws[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  {
-    uint32_t c = hist[(long long)t * nblk + blockIdx.x];
-    gbase[t] = hist_scan[(long long)t * nblk + blockIdx.x];
-    uint32_t ex = block_exclusive_scan(c, ws, nullptr);
-    dstart[t] = ex;
-    running[t] = 0;
+  {  // thread t owns digits t * PER .. t * PER + PER - 1 for the block-local scan
+    uint32_t c[PER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int d = t * PER + q;
+      c[q] = hist[(long long)d * nblk + blockIdx.x];
+      gbase[d] = hist_scan[(long long)d * nblk + blockIdx.x];
+      running[d] = 0;
+      sum += c[q];
+    }
+    uint32_t ex = block_exclusive_scan(sum, ws, nullptr);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      dstart[t * PER + q] = ex;
+      ex += c[q];
+    }
   }
   __syncthreads();
   for (int r = 0; r < kRadixRounds; ++r) {
 #pragma unroll
-    for (int q = 0; q < kRadixWarps; ++q) wcnt[q][t] = 0;
+    for (int q = 0; q < kRadixWarps; ++q)
+#pragma unroll
+      for (int p = 0; p < PER; ++p) wcnt[q][t + p * kRadixThreads] = 0;
     __syncthreads();
     int64_t i = base + r * kRadixThreads + t;
     bool ok = i < n;
     uint32_t key = ok ? kin[i] : 0u;
     uint32_t val = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
-    uint32_t d = ok ? ((key >> shift) & 255u) : (256u + lane);
+    uint32_t d = ok ? ((key >> shift) & MASK) : (uint32_t)(DIG + lane);
     unsigned peers = __match_any_sync(0xffffffffu, d);
     int rank_w = __popc(peers & ((1u << lane) - 1u));
     if (ok && rank_w == 0) wcnt[w][d] = __popc(peers);
     __syncthreads();
-    {  // prefix over warps for digit t, on top of the earlier rounds
-      uint32_t acc = running[t];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {  // prefix over warps for each owned digit
+      const int dd = t + p * kRadixThreads;
+      uint32_t acc = running[dd];
 #pragma unroll
       for (int q = 0; q < kRadixWarps; ++q) {
-        uint32_t c = wcnt[q][t];
-        wcnt[q][t] = acc;
+        uint32_t c = wcnt[q][dd];
+        wcnt[q][dd] = acc;
         acc += c;
       }
-      running[t] = acc;
+      running[dd] = acc;
     }
     __syncthreads();
     if (ok) {
@@ -179,7 +207,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
   const int64_t cnt = (n - base) < kRadixTile ? (n - base) : kRadixTile;
   for (int j = t; j < cnt; j += kRadixThreads) {
     uint32_t key = sk[j];
-    uint32_t d = (key >> shift) & 255u;
+    uint32_t d = (key >> shift) & MASK;
     uint32_t dst = gbase[d] + (j - dstart[d]);
     kout[dst] = key;
     vout[dst] = sv[j];
@@ -255,18 +283,33 @@ int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
   long long nblk = (n + kRadixTile - 1) / kRadixTile;
   if (nblk > c->hist_blocks_max) return PM_EINVAL;
   int cur = 0;
+  const int bits = c->radix_bits;
   for (int pass = 0; pass < c->radix_passes; ++pass) {
-    int shift = 8 * pass;
+    int shift = bits * pass;
     {
       LaunchScope L(c, s, K_RADIX_HIST);
-      k_radix_hist<<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
+      if (bits == 9)
+        k_radix_hist<9><<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
+      else
+        k_radix_hist<8><<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
     }
-    scan_exclusive(c, c->hist, c->hist_scan, 256 * nblk, s);
+    scan_exclusive(c, c->hist, c->hist_scan, (1LL << bits) * nblk, s);
     {
       LaunchScope L(c, s, K_RADIX_SCATTER);
-      k_radix_scatter<<<(unsigned)nblk, kRadixThreads, 0, s>>>(
-          c->keys[cur], pass == 0 ? nullptr : c->vals[cur], n, shift, nblk, c->hist,
-          c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
+      const uint32_t* vin = pass == 0 ? nullptr : c->vals[cur];
+      const int dyn = 2 * kRadixTile * (int)sizeof(uint32_t);
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_radix_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        cudaFuncSetAttribute(k_radix_scatter<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        attr = true;
+      }
+      if (bits == 9)
+        k_radix_scatter<9><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(
+            c->keys[cur], vin, n, shift, nblk, c->hist, c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
+      else
+        k_radix_scatter<8><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(
+            c->keys[cur], vin, n, shift, nblk, c->hist, c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
     }
     cur ^= 1;
   }

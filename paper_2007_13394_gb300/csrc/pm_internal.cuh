@@ -33,6 +33,8 @@ enum Kind {
   K_IC_ZA,
   K_IC_ASSEMBLE,
   K_REPACK,
+  K_FFT_X_FUSED,
+  K_READOUT3_KICK,
   K_NUM_KINDS
 };
 
@@ -73,10 +75,12 @@ struct pm_ctx {
   int nt = 0, ntl = 0;      // tiles per side and its log2
   long long nbuckets = 0;   // nt^3 * 8
   int radix_passes = 0;
+  int radix_bits = 8;       // digit width of the LSD radix passes
   int64_t n_max = 0;
   // meshes (two padded complex meshes, also viewed as padded real meshes)
   float2* meshA = nullptr;
   float2* meshB = nullptr;
+  float2* meshC = nullptr;  // third mesh: the fused force path (null: per-component path)
   // per-size tables: twiddles e^{-2 pi i t / n} (n entries), |k|^2, 1/sinc^4, k with Nyquist 0
   std::map<int, float2*> tw;
   float* ksq = nullptr;
@@ -152,6 +156,12 @@ void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, 
 void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* buf, int comp,
                            cudaStream_t s);
 void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
+// paint mesh in a (real) -> three real force meshes in a, b, cz
+void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz, cudaStream_t s);
+void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                   const float* mx, const float* my, const float* mz, int row_pitch, float K,
+                   float* p_out, float* f_out, uint32_t* u_out, uint32_t* id_out,
+                   const uint32_t* perm_scatter, cudaStream_t s);
 void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
                   const float* mesh, int row_pitch, int comp, float K, float* p_out, float* f_out,
                   uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter,

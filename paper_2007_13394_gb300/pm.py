@@ -126,6 +126,7 @@ class RunConfig:
     n_max: int = 0
     ns: float = 0.965
     sigma8: float = 0.81
+    flags: int = 0
     extra: dict = field(default_factory=dict)
 
     def n_cdm(self) -> int:
@@ -149,6 +150,7 @@ class RunConfig:
         c.a_ini_ode = self.a_ini_ode
         c.n_max = self.n_max or self.n_particles()
         c.ns, c.sigma8 = self.ns, self.sigma8
+        c.flags = self.flags
         return c
 
 

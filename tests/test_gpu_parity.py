@@ -28,9 +28,10 @@ def pm():
     return _pm
 
 
-def make_cfg(pm, nmesh=64, nc=32, nsites=8, box=128.0, nshell=4, nfib=1, m_nu=(0.2 / 3,) * 3, n_max=0):
+def make_cfg(pm, nmesh=64, nc=32, nsites=8, box=128.0, nshell=4, nfib=1, m_nu=(0.2 / 3,) * 3, n_max=0,
+             flags=0):
     return pm.RunConfig(box=box, nmesh=nmesh, nc=nc, nsites=nsites, nshell=nshell, nfib=nfib,
-                        m_nu=m_nu, n_max=n_max)
+                        m_nu=m_nu, n_max=n_max, flags=flags)
 
 
 def oracle_setup(cfg, a0=0.05, seed=1, kfs=0.0):
@@ -202,12 +203,14 @@ def test_readout_matches_oracle(pm):
 
 
 # ------------------------------------------------------------------ force
+@pytest.mark.parametrize("flags", [0, 1], ids=["fused_x", "per_component"])
 @pytest.mark.parametrize("size", ["cfg1", "cfg2_parity"])
-def test_force_relative_rms_below_1e5(pm, size):
+def test_force_relative_rms_below_1e5(pm, size, flags):
     if size == "cfg1":
-        cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3)
+        cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3, flags=flags)
     else:
-        cfg = make_cfg(pm, nmesh=256, nc=128, nsites=16, box=256.0, nshell=10, nfib=3, m_nu=(0.1 / 3,) * 3)
+        cfg = make_cfg(pm, nmesh=256, nc=128, nsites=16, box=256.0, nshell=10, nfib=3, m_nu=(0.1 / 3,) * 3,
+                       flags=flags)
     o = oracle_setup(cfg)
     ctx = pm.ParticleMesh(cfg)
     F = ctx.force(pm.as_u32_tensor(o["u"])).cpu().numpy().astype(np.float64)
@@ -229,8 +232,9 @@ def test_force_conserves_momentum(pm):
 
 
 # -------------------------------------------------------------------- step
-def test_step_matches_oracle(pm):
-    cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3)
+@pytest.mark.parametrize("flags", [0, 1], ids=["fused_x", "per_component"])
+def test_step_matches_oracle(pm, flags):
+    cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3, flags=flags)
     a0, a1 = 0.05, 0.07
     o = oracle_setup(cfg, a0=a0)
     ctx = pm.ParticleMesh(cfg)
