@@ -228,7 +228,7 @@ def run_ours(args):
     a_start = 0.01
     st = ctx.ic(noise, a_start, k_fs=workloads.free_streaming_k(cfg, a_start))
     del noise
-    sched = workloads.schedule_paper(max(25, args.warmup + args.steps + 2))
+    sched = workloads.schedule_paper(max(25, args.warmup + args.steps + 16))
     stream = torch.cuda.current_stream()
 
     def step(i):
@@ -267,6 +267,19 @@ def run_ours(args):
     launches = ctx.launch_count() - launches0
     dom = ctx.profile_read(reset=True).get(dominant, (0.0, 0))
     ctx.profile([])
+    # one more steady step with every kernel kind timed: per-kernel algorithmic bandwidth
+    peak_bw, _ = peaks()
+    ctx.profile(None)
+    ctx.profile_read(reset=True)
+    step(args.warmup + args.steps)
+    per_kind = {}
+    for kind, (kms, kn) in ctx.profile_read(reset=True).items():
+        alg_b = algorithmic_bytes(kind, cfg.nmesh, n)
+        per = kms / kn
+        per_kind[kind] = {"launches": kn, "ms_per_launch": round(per, 4),
+                          "gbs": round(alg_b / (per / 1e3) / 1e9, 1) if alg_b else None,
+                          "frac": round(alg_b / (per / 1e3) / 1e9 / peak_bw, 3) if alg_b else None}
+    ctx.profile([])
     ms_t = torch.tensor([ms], device="cuda")
     if world > 1:
         torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
@@ -290,7 +303,7 @@ def run_ours(args):
                 "step_share": shares[dominant] / sum(shares.values())}
         # end to end through the C-ABI with host buffers: copies in, step, copies out, every step
         e2e = None
-        if not args.no_e2e:
+        if not args.no_e2e and args.config != "cfg3":
             hu = pm.to_u32(st["u"]).copy()
             hp = st["p"].cpu().numpy().copy()
             hid = pm.to_u32(st["id"]).copy()
@@ -308,7 +321,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": 40 * n, "steps": k_e2e,
                    "note": "pm_step_host: u, p, id, f copied host->device, one KDK step, copied back"}
         cpu = None
-        if not args.no_cpu_baseline and world == 1:
+        if not args.no_cpu_baseline and world == 1 and args.config != "cfg3":
             ocfg, desc = oracle_sample_cfg(1)
             sec, n_o, cores = oracle_run(ocfg, 0, 1)
             cpu = {"value": n_o / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -326,7 +339,7 @@ def run_ours(args):
                              f"{cfg.nmesh ** 2 * (cfg.nmesh // 2 + 2) * 8 / 1e6:.0f} MB, particles "
                              f"{40 * n / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary(), "kernel_ms_first_step": {k: round(v, 4) for k, v in shares.items()},
+            "clocks": clk.summary(), "kernels_steady_step": per_kind,
         }
         print(json.dumps(out))
     ctx.close()

@@ -369,6 +369,7 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
     cudaMemcpy(c->winv, winv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     cudaMemcpy(c->kvec0, kv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
   }
+  tma_init(c);  // tensor maps for the TMA strided passes (classic kernels if unavailable)
   if (!twiddles(c, N)) {
     free_all(c);
     delete c;

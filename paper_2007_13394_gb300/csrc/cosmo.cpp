@@ -158,8 +158,30 @@ int Cosmo::init(const pm_config& c) {
   double d1, dp1;
   growth(1.0, &d1, &dp1);
   D1 = d1;
+  // node tables for the fast path: second derivative from the ODE, E^2 and its slope
+  tabDpp.assign(nsteps + 1, 0.0);
+  tabE2.assign(nsteps + 1, 0.0);
+  tabE2p.assign(nsteps + 1, 0.0);
+  for (int i = 0; i <= nsteps; ++i) {
+    const double lna = lna0 + i * dlna, a = std::exp(lna);
+    double y2[2] = {tabD[i], tabDp[i]}, dy[2];
+    rhs(lna, y2, dy);
+    tabDpp[i] = dy[1];
+    tabE2[i] = E2(a);
+    tabE2p[i] = 2.0 * tabE2[i] * dlnE_dlna(a);
+  }
+  fast = true;
   return PM_OK;
 }
+
+namespace {
+// cubic Hermite interpolation on [x0, x0 + h] from values and slopes at both ends
+inline double hermite(double t, double h, double f0, double d0, double f1, double d1) {
+  const double t2 = t * t, t3 = t2 * t;
+  return (2 * t3 - 3 * t2 + 1) * f0 + (t3 - 2 * t2 + t) * h * d0 + (-2 * t3 + 3 * t2) * f1 +
+         (t3 - t2) * h * d1;
+}
+}  // namespace
 
 double Cosmo::omega_nu_E2(double a) const {
   double s = 0.0;
@@ -180,7 +202,16 @@ double Cosmo::E2(double a) const {
   return omega_gamma / std::pow(a, 4) + omega_c / (a * a * a) + omega_nu_E2(a) + omega_lambda;
 }
 
-double Cosmo::E(double a) const { return std::sqrt(E2(a)); }
+double Cosmo::E(double a) const {
+  if (fast) {
+    const double x = std::log(a);
+    const double fi = (x - lna0) / dlna;
+    int i = (int)std::floor(fi);
+    if (i >= 0 && i < (int)tabE2.size() - 1)
+      return std::sqrt(hermite(fi - i, dlna, tabE2[i], tabE2p[i], tabE2[i + 1], tabE2p[i + 1]));
+  }
+  return std::sqrt(E2(a));
+}
 
 double Cosmo::dlnE_dlna(double a) const {
   double dE2 = -4.0 * omega_gamma / std::pow(a, 4) - 3.0 * omega_c / (a * a * a) +
@@ -209,6 +240,16 @@ void Cosmo::rk4(double lna, double hh, double y[2]) const {
 
 void Cosmo::growth(double a, double* Dv, double* Dp) const {
   double x = std::log(a);
+  if (fast) {  // Hermite on the RK4 grid: D from (D, D'), D' from (D', D'')
+    double fi = (x - lna0) / dlna;
+    int i = (int)std::floor(fi);
+    if (i < 0) i = 0;
+    if (i >= (int)tabD.size() - 1) i = (int)tabD.size() - 2;
+    const double t = fi - i;
+    *Dv = hermite(t, dlna, tabD[i], tabDp[i], tabD[i + 1], tabDp[i + 1]) / D1;
+    *Dp = hermite(t, dlna, tabDp[i], tabDpp[i], tabDp[i + 1], tabDpp[i + 1]) / D1;
+    return;
+  }
   double fi = (x - lna0) / dlna;
   int i = (int)std::floor(fi);
   if (i < 0) i = 0;

@@ -17,7 +17,9 @@ struct Cosmo {
   std::vector<int> mult;            // multiplicity of each distinct mass
   // growth table on a uniform grid in ln a
   double lna0 = 0, dlna = 0, D1 = 1;
-  std::vector<double> tabD, tabDp;
+  std::vector<double> tabD, tabDp, tabDpp;   // D, dD/dln a, d2D/dln a^2 at the grid nodes
+  std::vector<double> tabE2, tabE2p;         // E^2 and dE^2/dln a at the grid nodes
+  bool fast = false;                         // evaluate D, g_p, E from the tables
 
   int init(const pm_config& cfg);
   double E2(double a) const;

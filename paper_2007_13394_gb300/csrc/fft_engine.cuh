@@ -1,0 +1,170 @@
+// Stockham FFT engine shared by the FFT kernels (device code only).
+//
+// A line of M points (M a power of two, 16 <= M <= 2048) is held by M/16 threads,
+// 16 values each (value s of thread j is element j + s M/16).  Stockham stages of
+// radix 16 (the last stage radix 2..16) run in registers; between stages the line
+// goes through shared memory, padded by one float2 per 16 so that the stride-16
+// writes of the first stage are free of bank conflicts.  A line's elements may be
+// interleaved with other lines' (column stride cs in shared memory).  Twiddles
+// come from a table e^{-2 pi i t / TWN} computed in double precision on the host.
+#pragma once
+
+#include "pm_internal.cuh"
+
+namespace pmnu {
+namespace fft {
+
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// e^{s 2 pi i m / 16} for compile-time m, s = -1 forward, +1 inverse
+template <int m, bool INV>
+__device__ __forceinline__ float2 w16() {
+  constexpr float C[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                           0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                           -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                           0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+  constexpr float cv = C[m & 15];
+  constexpr float sv = C[(m + 12) & 15];  // sin(2 pi m / 16) = cos(2 pi (m - 4) / 16)
+  return INV ? make_float2(cv, sv) : make_float2(cv, -sv);
+}
+
+template <int m, bool INV>
+__device__ __forceinline__ float2 rot16(float2 a) {
+  if constexpr ((m & 15) == 0) {
+    return a;
+  } else if constexpr ((m & 15) == 4) {  // multiply by -i (forward) or +i (inverse)
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  } else if constexpr ((m & 15) == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr ((m & 15) == 12) {
+    return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+  } else {
+    return cmul(a, w16<m, INV>());
+  }
+}
+
+template <int R>
+__host__ __device__ constexpr int brev(int i) {
+  int r = 0;
+  for (int b = 1, k = R >> 1; b < R; b <<= 1, k >>= 1)
+    if (i & b) r |= k;
+  return r;
+}
+
+// In-register DFT of size R (2, 4, 8, 16): radix-2 decimation in time.
+template <int R, bool INV, int LEN = 2>
+__device__ __forceinline__ void dft_layers(float2 (&x)[R]);
+
+template <int R, bool INV, int LEN, int I, int K>
+__device__ __forceinline__ void dft_bfly(float2 (&x)[R]) {
+  if constexpr (I < R) {
+    if constexpr (K < LEN / 2) {
+      float2 a = x[I + K];
+      float2 b = rot16<K * (16 / LEN), INV>(x[I + K + LEN / 2]);
+      x[I + K] = cadd(a, b);
+      x[I + K + LEN / 2] = csub(a, b);
+      dft_bfly<R, INV, LEN, I, K + 1>(x);
+    } else {
+      dft_bfly<R, INV, LEN, I + LEN, 0>(x);
+    }
+  }
+}
+
+template <int R, bool INV, int LEN>
+__device__ __forceinline__ void dft_layers(float2 (&x)[R]) {
+  if constexpr (LEN <= R) {
+    dft_bfly<R, INV, LEN, 0, 0>(x);
+    dft_layers<R, INV, LEN * 2>(x);
+  }
+}
+
+template <int R, int I>
+__device__ __forceinline__ void bitrev_perm(float2 (&x)[R]) {
+  if constexpr (I < R) {
+    constexpr int J = brev<R>(I);
+    if constexpr (J > I) {
+      float2 t = x[I];
+      x[I] = x[J];
+      x[J] = t;
+    }
+    bitrev_perm<R, I + 1>(x);
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2 (&x)[R]) {
+  bitrev_perm<R, 0>(x);
+  dft_layers<R, INV, 2>(x);
+}
+
+// One Stockham stage on a line of M points (sub-transform length NS, radix R).
+template <int M, int TWN, int NS, int R, bool INV, bool LAST>
+__device__ __forceinline__ void stage(float2 (&v)[16], int j, float2* sm, int cs,
+                                      const float2* __restrict__ tw) {
+  constexpr int B = 16 / R;  // butterflies per thread
+  constexpr int Q = M / 16;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int jj = j + b * Q;
+    const int k = jj & (NS - 1);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[b + r * B];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(tw + ((k * r * (TWN / (NS * R))) & (TWN - 1)));
+        x[r] = cmul(x[r], INV ? cconj(w) : w);
+      }
+    }
+    dft<R, INV>(x);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * B] = x[r];
+    } else {
+      const int base = (jj / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    __syncthreads();
+  }
+}
+
+template <int M, int TWN, int NS, bool INV>
+__device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, int cs,
+                                           const float2* __restrict__ tw) {
+  constexpr int REM = M / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr bool LAST = (NS * R == M);
+  stage<M, TWN, NS, R, INV, LAST>(v, j, sm, cs, tw);
+  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV>(v, j, sm, cs, tw);
+}
+
+// Fused epilogue / prologue of the x pass.
+struct KTables {
+  const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)
+  const float* winv;   // 1 / sinc^4(pi n_s / N)
+  const float* kvec0;  // k_n with the Nyquist index set to 0
+  float gcoef;         // -1.5 Omega_m0 / N^3
+};
+
+enum { EPI_NONE = 0, EPI_GREEN = 1 };
+enum { PRO_NONE = 0, PRO_GRAD = 1 };
+
+enum { MODE_PLAIN = 0, MODE_GREEN = 1, MODE_GRAD = 2, MODE_FUSED = 3 };
+
+}  // namespace fft
+
+// TMA-pipelined strided pass over one of the context's force meshes (k_fft_tma.cu);
+// returns PM_EINVAL when it does not apply (no tensor maps, foreign buffer or size),
+// so the caller runs the classic kernel instead.
+int strided_tma(pm_ctx* c, const Geom& g, const float2* src, float2* d0, float2* d1, float2* d2,
+                int axis, bool inv, int mode, int comp, const float2* tw, const fft::KTables& kt,
+                cudaStream_t s);
+
+}  // namespace pmnu

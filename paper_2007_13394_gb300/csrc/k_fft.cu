@@ -20,142 +20,14 @@
 // so each global access covers TK consecutive float2.
 #include <cuda_runtime.h>
 
+#include "fft_engine.cuh"
 #include "pm_internal.cuh"
 
 namespace pmnu {
 
 namespace {
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-
-// e^{s 2 pi i m / 16} for compile-time m, s = -1 forward, +1 inverse
-template <int m, bool INV>
-__device__ __forceinline__ float2 w16() {
-  constexpr float C[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
-                           0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
-                           -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
-                           0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
-  constexpr float cv = C[m & 15];
-  constexpr float sv = C[(m + 12) & 15];  // sin(2 pi m / 16) = cos(2 pi (m - 4) / 16)
-  return INV ? make_float2(cv, sv) : make_float2(cv, -sv);
-}
-
-template <int m, bool INV>
-__device__ __forceinline__ float2 rot16(float2 a) {
-  if constexpr ((m & 15) == 0) {
-    return a;
-  } else if constexpr ((m & 15) == 4) {  // multiply by -i (forward) or +i (inverse)
-    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-  } else if constexpr ((m & 15) == 8) {
-    return make_float2(-a.x, -a.y);
-  } else if constexpr ((m & 15) == 12) {
-    return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
-  } else {
-    return cmul(a, w16<m, INV>());
-  }
-}
-
-template <int R>
-__host__ __device__ constexpr int brev(int i) {
-  int r = 0;
-  for (int b = 1, k = R >> 1; b < R; b <<= 1, k >>= 1)
-    if (i & b) r |= k;
-  return r;
-}
-
-// In-register DFT of size R (2, 4, 8, 16): radix-2 decimation in time.
-template <int R, bool INV, int LEN = 2>
-__device__ __forceinline__ void dft_layers(float2 (&x)[R]);
-
-template <int R, bool INV, int LEN, int I, int K>
-__device__ __forceinline__ void dft_bfly(float2 (&x)[R]) {
-  if constexpr (I < R) {
-    if constexpr (K < LEN / 2) {
-      float2 a = x[I + K];
-      float2 b = rot16<K * (16 / LEN), INV>(x[I + K + LEN / 2]);
-      x[I + K] = cadd(a, b);
-      x[I + K + LEN / 2] = csub(a, b);
-      dft_bfly<R, INV, LEN, I, K + 1>(x);
-    } else {
-      dft_bfly<R, INV, LEN, I + LEN, 0>(x);
-    }
-  }
-}
-
-template <int R, bool INV, int LEN>
-__device__ __forceinline__ void dft_layers(float2 (&x)[R]) {
-  if constexpr (LEN <= R) {
-    dft_bfly<R, INV, LEN, 0, 0>(x);
-    dft_layers<R, INV, LEN * 2>(x);
-  }
-}
-
-template <int R, int I>
-__device__ __forceinline__ void bitrev_perm(float2 (&x)[R]) {
-  if constexpr (I < R) {
-    constexpr int J = brev<R>(I);
-    if constexpr (J > I) {
-      float2 t = x[I];
-      x[I] = x[J];
-      x[J] = t;
-    }
-    bitrev_perm<R, I + 1>(x);
-  }
-}
-
-template <int R, bool INV>
-__device__ __forceinline__ void dft(float2 (&x)[R]) {
-  bitrev_perm<R, 0>(x);
-  dft_layers<R, INV, 2>(x);
-}
-
-// One Stockham stage on a line of M points (sub-transform length NS, radix R).
-template <int M, int TWN, int NS, int R, bool INV, bool LAST>
-__device__ __forceinline__ void stage(float2 (&v)[16], int j, float2* sm, int cs,
-                                      const float2* __restrict__ tw) {
-  constexpr int B = 16 / R;  // butterflies per thread
-  constexpr int Q = M / 16;
-#pragma unroll
-  for (int b = 0; b < B; ++b) {
-    const int jj = j + b * Q;
-    const int k = jj & (NS - 1);
-    float2 x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = v[b + r * B];
-    if constexpr (NS > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(tw + ((k * r * (TWN / (NS * R))) & (TWN - 1)));
-        x[r] = cmul(x[r], INV ? cconj(w) : w);
-      }
-    }
-    dft<R, INV>(x);
-    if constexpr (LAST) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) v[b + r * B] = x[r];
-    } else {
-      const int base = (jj / NS) * NS * R + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
-    }
-  }
-  if constexpr (!LAST) {
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
-    __syncthreads();
-  }
-}
-
-template <int M, int TWN, int NS, bool INV>
-__device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, int cs,
-                                           const float2* __restrict__ tw) {
-  constexpr int REM = M / NS;
-  constexpr int R = REM >= 16 ? 16 : REM;
-  constexpr bool LAST = (NS * R == M);
-  stage<M, TWN, NS, R, INV, LAST>(v, j, sm, cs, tw);
-  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV>(v, j, sm, cs, tw);
-}
+using namespace fft;
 
 constexpr int kZThreads = 256;
 
@@ -228,16 +100,7 @@ __global__ void __launch_bounds__(kZThreads, 4) k_fft_z_c2r(float2* __restrict__
   for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
 }
 
-// Fused epilogue / prologue of the x pass.
-struct KTables {
-  const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)
-  const float* winv;   // 1 / sinc^4(pi n_s / N)
-  const float* kvec0;  // k_n with the Nyquist index set to 0
-  float gcoef;         // -1.5 Omega_m0 / N^3
-};
 
-enum { EPI_NONE = 0, EPI_GREEN = 1 };
-enum { PRO_NONE = 0, PRO_GRAD = 1 };
 
 // Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK).
 // 64 registers a thread: two 512-thread CTAs (or four of 256) resident per SM
@@ -433,6 +296,15 @@ void dispatch_strided(const Geom& g, const float2* src, float2* dst, int axis, c
   }
 }
 
+// Strided pass: the TMA-pipelined kernel when it applies, else the classic one.
+template <bool INV, int EPI, int PRO>
+void strided(pm_ctx* c, const Geom& g, const float2* src, float2* dst, int axis, const float2* tw,
+             const KTables& kt, int comp, cudaStream_t s) {
+  const int mode = EPI == EPI_GREEN ? MODE_GREEN : (PRO == PRO_GRAD ? MODE_GRAD : MODE_PLAIN);
+  if (strided_tma(c, g, src, dst, nullptr, nullptr, axis, INV, mode, comp, tw, kt, s) == PM_OK) return;
+  dispatch_strided<INV, EPI, PRO>(g, src, dst, axis, tw, kt, comp, s);
+}
+
 KTables ktables(pm_ctx* c, const Geom& g) {
   KTables kt;
   kt.ksq = c->ksq;
@@ -454,14 +326,14 @@ void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, 
   }
   {
     LaunchScope L(c, s, K_FFT_Y);
-    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+    strided<false, EPI_NONE, PRO_NONE>(c, g, buf, buf, 1, tw, kt, 0, s);
   }
   if (green) {
     LaunchScope L(c, s, K_FFT_X_GREEN);
-    dispatch_strided<false, EPI_GREEN, PRO_NONE>(g, buf, dst, 0, tw, kt, 0, s);
+    strided<false, EPI_GREEN, PRO_NONE>(c, g, buf, dst, 0, tw, kt, 0, s);
   } else {
     LaunchScope L(c, s, K_FFT_X_PLAIN);
-    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, buf, dst, 0, tw, kt, 0, s);
+    strided<false, EPI_NONE, PRO_NONE>(c, g, buf, dst, 0, tw, kt, 0, s);
   }
 }
 
@@ -471,11 +343,11 @@ void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* 
   KTables kt = ktables(c, g);
   {
     LaunchScope L(c, s, K_FFT_X_GRAD);
-    dispatch_strided<true, EPI_NONE, PRO_GRAD>(g, phi, buf, 0, tw, kt, comp, s);
+    strided<true, EPI_NONE, PRO_GRAD>(c, g, phi, buf, 0, tw, kt, comp, s);
   }
   {
     LaunchScope L(c, s, K_FFT_Y);
-    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+    strided<true, EPI_NONE, PRO_NONE>(c, g, buf, buf, 1, tw, kt, 0, s);
   }
   {
     LaunchScope L(c, s, K_FFT_Z_C2R);
@@ -492,10 +364,11 @@ void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz,
   }
   {
     LaunchScope L(c, s, K_FFT_Y);
-    dispatch_strided<false, EPI_NONE, PRO_NONE>(g, a, a, 1, tw, kt, 0, s);
+    strided<false, EPI_NONE, PRO_NONE>(c, g, a, a, 1, tw, kt, 0, s);
   }
   {
     LaunchScope L(c, s, K_FFT_X_FUSED);
+    if (strided_tma(c, g, a, a, b, cz, 0, false, MODE_FUSED, 0, tw, kt, s) == PM_OK) goto fused_done;
     switch (g.logn) {
       case 5: launch_x_fused<5>(a, b, cz, g.pc, tw, kt, s); break;
       case 6: launch_x_fused<6>(a, b, cz, g.pc, tw, kt, s); break;
@@ -506,12 +379,13 @@ void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz,
       case 11: launch_x_fused<11>(a, b, cz, g.pc, tw, kt, s); break;
       default: break;
     }
+  fused_done:;
   }
   float2* bufs[3] = {a, b, cz};
   for (int comp = 0; comp < 3; ++comp) {
     {
       LaunchScope L(c, s, K_FFT_Y);
-      dispatch_strided<true, EPI_NONE, PRO_NONE>(g, bufs[comp], bufs[comp], 1, tw, kt, 0, s);
+      strided<true, EPI_NONE, PRO_NONE>(c, g, bufs[comp], bufs[comp], 1, tw, kt, 0, s);
     }
     {
       LaunchScope L(c, s, K_FFT_Z_C2R);
@@ -525,11 +399,11 @@ void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s) {
   KTables kt = ktables(c, g);
   {
     LaunchScope L(c, s, K_FFT_X_PLAIN);
-    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 0, tw, kt, 0, s);
+    strided<true, EPI_NONE, PRO_NONE>(c, g, buf, buf, 0, tw, kt, 0, s);
   }
   {
     LaunchScope L(c, s, K_FFT_Y);
-    dispatch_strided<true, EPI_NONE, PRO_NONE>(g, buf, buf, 1, tw, kt, 0, s);
+    strided<true, EPI_NONE, PRO_NONE>(c, g, buf, buf, 1, tw, kt, 0, s);
   }
   {
     LaunchScope L(c, s, K_FFT_Z_C2R);

@@ -1,6 +1,7 @@
 // Internal context, launch bookkeeping and small device helpers of libpmnu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,6 +82,9 @@ struct pm_ctx {
   float2* meshA = nullptr;
   float2* meshB = nullptr;
   float2* meshC = nullptr;  // third mesh: the fused force path (null: per-component path)
+  // tensor maps of meshA/B/C for the TMA strided passes: [mesh][0: x-pass box, 1: y-pass box]
+  CUtensorMap tmap[3][2];
+  bool tma_ok = false;
   // per-size tables: twiddles e^{-2 pi i t / n} (n entries), |k|^2, 1/sinc^4, k with Nyquist 0
   std::map<int, float2*> tw;
   float* ksq = nullptr;
@@ -176,6 +180,7 @@ int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* 
               double* P_out, int64_t* nmodes_out, cudaStream_t s);
 int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s);
 float2* twiddles(pm_ctx* c, int n);
+bool tma_init(pm_ctx* c);
 
 #define PM_CUDA_TRY(expr)                      \
   do {                                         \
