@@ -143,6 +143,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def aggregate_replicas(ms_local, n_local, world, device="cpu"):
+    """Replicas only: every rank ran its own problem.  Returns (ms_max, total particles,
+    updates per second) -- the slowest rank's step time over all ranks' particles."""
+    import torch
+    t = torch.tensor([ms_local, float(n_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms_max, n_tot = float(mx.item()), float(tot.item())
+    else:
+        ms_max, n_tot = ms_local, float(n_local)
+    return ms_max, int(n_tot), n_tot / (ms_max / 1e3)
+
+
 # --------------------------------------------------------------- oracle arm
 def oracle_sample_cfg(steps_total, budget_s=120.0):
     """A bounded sample of the cfg2 workload: same 2 Mpc/h spacing, boost-2 mesh and
@@ -280,11 +297,7 @@ def run_ours(args):
                           "gbs": round(alg_b / (per / 1e3) / 1e9, 1) if alg_b else None,
                           "frac": round(alg_b / (per / 1e3) / 1e9 / peak_bw, 3) if alg_b else None}
     ctx.profile([])
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = n * world / (ms_max / 1e3)
+    ms_max, n_total, value = aggregate_replicas(ms, n, world, device="cuda")
 
     out = None
     if rank == 0:
