@@ -114,6 +114,7 @@ def algorithmic_bytes(kind, n_mesh, n_particles):
         "fft_x_fused": 4 * half,                                # read once, three components written
         # u, p, id read; p, f, u, id written (tile order); three meshes read once
         "readout3_kick": 68 * n_particles + 12 * cells,
+        "fft_x_plain": 2 * half,
         "kick_drift_keys": 64 * n_particles,
         "gather": 64 * n_particles,
         "radix_scatter": 16 * n_particles,
@@ -238,6 +239,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     cfg = workloads.PRESETS[args.config]()
+    if args.two_mesh:
+        cfg.flags |= 1
     ctx = pm.ParticleMesh(cfg)
     n = cfg.n_particles()
     # initial conditions on the GPU from seeded white noise (one independent replica per rank)
@@ -316,7 +319,7 @@ def run_ours(args):
                 "step_share": shares[dominant] / sum(shares.values())}
         # end to end through the C-ABI with host buffers: copies in, step, copies out, every step
         e2e = None
-        if not args.no_e2e and args.config != "cfg3":
+        if not args.no_e2e and args.config not in ("cfg3", "cfg_mid"):
             hu = pm.to_u32(st["u"]).copy()
             hp = st["p"].cpu().numpy().copy()
             hid = pm.to_u32(st["id"]).copy()
@@ -334,7 +337,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": 40 * n, "steps": k_e2e,
                    "note": "pm_step_host: u, p, id, f copied host->device, one KDK step, copied back"}
         cpu = None
-        if not args.no_cpu_baseline and world == 1 and args.config != "cfg3":
+        if not args.no_cpu_baseline and world == 1 and args.config not in ("cfg3", "cfg_mid"):
             ocfg, desc = oracle_sample_cfg(1)
             sec, n_o, cores = oracle_run(ocfg, 0, 1)
             cpu = {"value": n_o / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -367,7 +370,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg3"], default="cfg2")
+    ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg_mid", "cfg3"], default="cfg2")
+    ap.add_argument("--two-mesh", action="store_true", help="per-component force path (flags bit 0)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

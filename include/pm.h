@@ -38,7 +38,7 @@
  *
  * Memory and ownership: every particle and output array passed in is owned
  * by the caller; a context owns its scratch (three padded complex meshes of
- * N * N * (N/2 + 2) float2 each -- two with flags bit 0 -- plus sort buffers for
+ * N * N * (N/2 + 2) float2 each -- two with flags bit 0 or nmesh 2048 -- plus sort buffers for
  * n_max particles).
  * Arrays are structure-of-arrays: u[3 * n] holds the x plane, then y, then z.
  * "Device" pointers are CUDA device memory of the context's device; "host"
@@ -94,7 +94,8 @@ typedef struct pm_config {
   int64_t n_max;       /* capacity of the sort scratch (>= every n passed later) */
   double ns;           /* spectral index of the synthetic initial spectrum (pm_ic) */
   double sigma8;       /* normalisation of the synthetic initial spectrum (pm_ic) */
-  uint32_t flags;      /* bit 0: two-mesh per-component force path (less memory); other bits 0 */
+  uint32_t flags;      /* bit 0: two-mesh per-component force path (less memory; always used
+                          for nmesh = 2048); other bits 0 */
   int32_t pad1;
 } pm_config;
 

@@ -332,7 +332,9 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
     for (long long m = scan_n; m > 1; m = (m + 4095) / 4096) need += 2 * (size_t)((m + 4095) / 4096);
     c->scan_tmp_elems = need;
   }
-  const bool two_mesh = (cfg->flags & 1u) != 0;  // flag bit 0: per-component force path
+  // flag bit 0, or a 2048^3 mesh: per-component force path with two meshes (at 2048^3 it is
+  // also the faster one: reading three 34 GB meshes at once starves the readout)
+  const bool two_mesh = (cfg->flags & 1u) != 0 || N >= 2048;
   if ((!two_mesh && dalloc(&c->meshC, me)) || dalloc(&c->meshA, me) || dalloc(&c->meshB, me) ||
       dalloc(&c->ksq, N) ||
       dalloc(&c->winv, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||

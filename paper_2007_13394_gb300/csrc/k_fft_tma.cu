@@ -307,7 +307,9 @@ int strided_tma(pm_ctx* c, const Geom& g, const float2* src, float2* d0, float2*
                 cudaStream_t s) {
   using namespace fft;
   if (!c->tma_ok || g.n != c->g.n) return PM_EINVAL;
-  if (g.logn >= 11) return PM_EINVAL;  // 2048-point columns: two-column tiles, classic kernels
+  // Columns of 1024 or more points only fit 2- or 4-column tiles (16-32 B rows), which the
+  // TMA engine serves far below the classic kernels' rate: TMA for up to 512 points.
+  if (g.logn >= 10) return PM_EINVAL;
   const int bi = mesh_index(c, src);
   if (bi < 0) return PM_EINVAL;
   const CUtensorMap* map = &c->tmap[bi][axis == 1 ? 1 : 0];

@@ -22,43 +22,6 @@ constexpr int kTileCells = kTile * kTile * kTile;  // 4096
 constexpr float kFix = 4294967296.0f;              // 2^32
 constexpr float kUnfix = 2.3283064365386963e-10f;  // 2^-32
 
-__device__ __forceinline__ void paint_one(long long* acc, uint32_t ux, uint32_t uy, uint32_t uz,
-                                          float m, int shift, int n, int ox, int oy, int oz,
-                                          float fscale, uint32_t fmask) {
-  int c[3] = {(int)(ux >> shift), (int)(uy >> shift), (int)(uz >> shift)};
-  int o[3] = {ox, oy, oz};
-  float f[3] = {(float)(ux & fmask) * fscale, (float)(uy & fmask) * fscale,
-                (float)(uz & fmask) * fscale};
-  int l[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int v = c[d] - o[d];  // local coordinate relative to the tile origin
-    if (v > n / 2) v -= n;
-    if (v < -n / 2) v += n;
-    l[d] = v;
-  }
-#pragma unroll
-  for (int bx = 0; bx < 2; ++bx) {
-    int lx = l[0] + bx;
-    if (lx < 0 || lx >= kTile) continue;
-    float wx = bx ? f[0] : 1.0f - f[0];
-#pragma unroll
-    for (int by = 0; by < 2; ++by) {
-      int ly = l[1] + by;
-      if (ly < 0 || ly >= kTile) continue;
-      float wxy = wx * (by ? f[1] : 1.0f - f[1]);
-#pragma unroll
-      for (int bz = 0; bz < 2; ++bz) {
-        int lz = l[2] + bz;
-        if (lz < 0 || lz >= kTile) continue;
-        float w = wxy * (bz ? f[2] : 1.0f - f[2]) * m;
-        long long q = __float2ll_rn(w * kFix);
-        atomicAdd((unsigned long long*)&acc[(lx * kTile + ly) * kTile + lz], (unsigned long long)q);
-      }
-    }
-  }
-}
-
 // The 14 bucket runs a tile reads, as (neighbour offset o, first class, end class):
 // its own tile (all classes), then for each low-side neighbour o the classes that
 // contain every bit of o, merged where they are contiguous.
@@ -66,14 +29,20 @@ __constant__ int8_t c_runs[14][3] = {{0, 0, 8}, {4, 4, 8}, {2, 2, 4}, {2, 6, 8},
                                      {1, 3, 4}, {1, 5, 6}, {1, 7, 8}, {6, 6, 8}, {5, 5, 6},
                                      {5, 7, 8}, {3, 3, 4}, {3, 7, 8}, {7, 7, 8}};
 
+// Shared accumulator layout: cell (x, y, z) of the tile at x * kSx + y * kSy + z.  With
+// kSy = 18 and kSx = 292 (4 and 2 modulo 16) the 8 CIC corners of one particle land in
+// 8 distinct 8-byte bank pairs.
+constexpr int kSy = 18, kSx = 292;
+constexpr int kAccWords = kTile * kSx;
+
 __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
     int nm, int shift, int ntl, int row_pitch, int* __restrict__ err) {
-  __shared__ long long acc[kTileCells];
+  __shared__ long long acc[kAccWords];
   __shared__ uint32_t run_lo[14], run_pre[15];
   const int t = threadIdx.x;
-  for (int i = t; i < kTileCells; i += kPaintThreads) acc[i] = 0;
+  for (int i = t; i < kAccWords; i += kPaintThreads) acc[i] = 0;
   const int nt = 1 << ntl;
   const uint32_t tile = blockIdx.x;
   const int tx = tile >> (2 * ntl), ty = (tile >> ntl) & (nt - 1), tz = tile & (nt - 1);
@@ -103,27 +72,67 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   const float fscale = 1.0f / (float)(1u << shift);
   const uint32_t fmask = (1u << shift) - 1u;
   const uint32_t total = run_pre[14];
+  // A warp takes 32 particles per round, one per lane (coalesced loads), then paints them
+  // in 8 sub-rounds of 4: lane = 8 * (particle slot) + corner (bx, by, bz), the particle's
+  // data broadcast by shuffles.  A particle's 8 corners hit 8 distinct bank pairs.
+  const int lane = t & 31, warp = t >> 5;
+  const int bx = (lane >> 2) & 1, by = (lane >> 1) & 1, bz = lane & 1;
+  const int corner_off = bx * kSx + by * kSy + bz;
+  const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
   bool bad = false;
   int r = 0;
-  for (uint32_t v = t; v < total; v += kPaintThreads) {
-    while (v >= run_pre[r + 1]) ++r;   // v only grows, so the run index only grows
-    const uint32_t k = run_lo[r] + (v - run_pre[r]);
-    float m = id_mass(mt, ids[k], species, &bad);
-    if (m == 0.0f) continue;
-    paint_one(acc, us[k], us[n + k], us[2 * n + k], m, shift, nm, tx * kTile, ty * kTile,
-              tz * kTile, fscale, fmask);
+  for (uint32_t base = warp * 32; base < total; base += kPaintThreads) {
+    const uint32_t v = base + lane;
+    int cell = -1;                    // packed local cell (x * kSx + y * kSy + z) of the lower corner
+    float fx = 0.f, fy = 0.f, fz = 0.f, m = 0.f;
+    int lo_ok = 0;                    // bit d: lower corner inside along d; bit 3 + d: upper inside
+    if (v < total) {
+      while (v >= run_pre[r + 1]) ++r;  // v only grows, so the run index only grows
+      const uint32_t k = run_lo[r] + (v - run_pre[r]);
+      m = id_mass(mt, ids[k], species, &bad);
+      const uint32_t u0 = us[k], u1 = us[n + k], u2 = us[2 * n + k];
+      int l[3] = {(int)(u0 >> shift) - ox, (int)(u1 >> shift) - oy, (int)(u2 >> shift) - oz};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {  // periodic wrap relative to the tile origin
+        if (l[d] > nm / 2) l[d] -= nm;
+        if (l[d] < -nm / 2) l[d] += nm;
+        if (l[d] >= 0 && l[d] < kTile) lo_ok |= 1 << d;
+        if (l[d] + 1 >= 0 && l[d] + 1 < kTile) lo_ok |= 8 << d;
+      }
+      cell = l[0] * kSx + l[1] * kSy + l[2];
+      fx = (float)(u0 & fmask) * fscale;
+      fy = (float)(u1 & fmask) * fscale;
+      fz = (float)(u2 & fmask) * fscale;
+    }
+#pragma unroll
+    for (int sub = 0; sub < 8; ++sub) {
+      const int src = sub * 4 + (lane >> 3);
+      const int c_s = __shfl_sync(0xffffffffu, cell, src);
+      const int ok_s = __shfl_sync(0xffffffffu, lo_ok, src);
+      const float fx_s = __shfl_sync(0xffffffffu, fx, src);
+      const float fy_s = __shfl_sync(0xffffffffu, fy, src);
+      const float fz_s = __shfl_sync(0xffffffffu, fz, src);
+      const float m_s = __shfl_sync(0xffffffffu, m, src);
+      const bool inside = ((ok_s >> (bx ? 3 : 0)) & 1) && ((ok_s >> (by ? 4 : 1)) & 1) &&
+                          ((ok_s >> (bz ? 5 : 2)) & 1);
+      if (m_s != 0.0f && inside) {
+        const float w =
+            (bx ? fx_s : 1.0f - fx_s) * (by ? fy_s : 1.0f - fy_s) * (bz ? fz_s : 1.0f - fz_s) * m_s;
+        const long long q = __float2ll_rn(w * kFix);
+        atomicAdd((unsigned long long*)&acc[c_s + corner_off], (unsigned long long)q);
+      }
+    }
   }
   if (bad) atomicOr(err, 1);
   __syncthreads();
   // write the tile: 256 rows of 16 floats, as float4
-  for (int q = t; q < kTileCells / 4; q += kPaintThreads) {
+  for (int q = t; q < kTile * kTile * kTile / 4; q += kPaintThreads) {
     int row = q >> 2, z4 = (q & 3) * 4;
     int lx = row >> 4, ly = row & 15;
-    const long long* a = &acc[(lx * kTile + ly) * kTile + z4];
+    const long long* a = &acc[lx * kSx + ly * kSy + z4];
     float4 v = make_float4(__ll2float_rn(a[0]) * kUnfix, __ll2float_rn(a[1]) * kUnfix,
                            __ll2float_rn(a[2]) * kUnfix, __ll2float_rn(a[3]) * kUnfix);
-    size_t off = ((size_t)(tx * kTile + lx) * nm + (ty * kTile + ly)) * (size_t)row_pitch +
-                 tz * kTile + z4;
+    size_t off = ((size_t)(ox + lx) * nm + (oy + ly)) * (size_t)row_pitch + oz + z4;
     *reinterpret_cast<float4*>(mesh + off) = v;
   }
 }

@@ -34,7 +34,14 @@ def cfg3() -> RunConfig:
                      m_nu=(0.19786, 0.19805, 0.20408))
 
 
-PRESETS = {"cfg1": cfg1, "cfg2": cfg2, "cfg2_parity": cfg2_parity, "cfg3": cfg3}
+def cfg_mid() -> RunConfig:
+    """1024 Mpc/h, 512^3 CDM + 64^3 x 70 neutrinos (M_nu = 0.6 eV hierarchy), mesh 1024^3: the
+    cfg3 density and boost at one eighth of the volume."""
+    return RunConfig(box=1024.0, nmesh=1024, nc=512, nsites=64, nshell=10, nfib=3,
+                     m_nu=(0.19786, 0.19805, 0.20408))
+
+
+PRESETS = {"cfg1": cfg1, "cfg2": cfg2, "cfg2_parity": cfg2_parity, "cfg_mid": cfg_mid, "cfg3": cfg3}
 
 
 def schedule_linear(a0: float, a1: float, n: int):
