@@ -201,6 +201,15 @@ int pm_power(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int3
  * Writes st->u, st->p, st->id (canonical order), st->n, st->a = a0, st->f_valid = 0. */
 int pm_ic(pm_ctx* ctx, const float* noise, double a0, double k_fs, pm_state* st, void* stream);
 
+/* Checkpoint of a particle state (per-step checkpoints for resuming and for the
+ * adjoint).  File: a 512-byte ASCII JSON header padded with spaces ({"format":
+ * "pmnu-state-1", "n", "a", "f_valid", "nmesh", "box", "config_hash"}), then u[3n]
+ * uint32, p[3n] float32, id[n] uint32, f[3n] float32, little-endian.  Synchronous.
+ * pm_state_load checks format, n and the configuration hash (PM_EINVAL on a mismatch)
+ * and fills the caller's device arrays (st->n must equal the file's n). */
+int pm_state_save(pm_ctx* ctx, const pm_state* st, const char* path);
+int pm_state_load(pm_ctx* ctx, pm_state* st, const char* path);
+
 /* ---- stage-level entry points (device arrays; for testing each kernel) ------- */
 
 /* Forward r2c FFT (unnormalised, e^{-ikx}) of a real N^3 mesh: out holds

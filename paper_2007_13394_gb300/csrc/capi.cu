@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -537,6 +538,100 @@ int pm_ic(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, v
   if (!valid(c)) return PM_ENOTINIT;
   if (!noise || !st || !st->u || !st->p || !st->id) return PM_EINVAL;
   return ic_build(c, noise, a0, k_fs, st, S(stream));
+}
+
+namespace {
+// FNV-1a over the fields that define the physics and the mesh
+uint64_t config_hash(const pm_config& f) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(&f.box, 8); mix(&f.nmesh, 4); mix(&f.nc, 4); mix(&f.nsites, 4); mix(&f.nshell, 4);
+  mix(&f.nfib, 4); mix(&f.h, 8); mix(&f.omega_m, 8); mix(&f.t_cmb, 8); mix(&f.n_eff, 8);
+  mix(&f.n_nu, 4); mix(f.m_nu, 24); mix(&f.a_ini_ode, 8);
+  return h;
+}
+constexpr size_t kHeader = 512;
+}  // namespace
+
+int pm_state_save(pm_ctx* c, const pm_state* st, const char* path) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!st || !path || st->n < 0 || (st->n > 0 && (!st->u || !st->p || !st->id || !st->f))) return PM_EINVAL;
+  const int64_t n = st->n;
+  std::vector<char> buf(kHeader + (size_t)n * 40);
+  char hdr[kHeader];
+  std::memset(hdr, ' ', kHeader);
+  int len = std::snprintf(hdr, kHeader,
+                          "{\"format\": \"pmnu-state-1\", \"n\": %lld, \"a\": %.17g, \"f_valid\": %d, "
+                          "\"nmesh\": %d, \"box\": %.17g, \"config_hash\": \"%016llx\"}",
+                          (long long)n, st->a, st->f_valid, c->cfg.nmesh, c->cfg.box,
+                          (unsigned long long)config_hash(c->cfg));
+  if (len <= 0 || len >= (int)kHeader - 1) return PM_EINVAL;
+  hdr[len] = ' ';
+  hdr[kHeader - 1] = '\n';
+  std::memcpy(buf.data(), hdr, kHeader);
+  char* d = buf.data() + kHeader;
+  if (n > 0) {
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    PM_CUDA_TRY(cudaMemcpy(d, st->u, 12 * n, cudaMemcpyDeviceToHost));
+    PM_CUDA_TRY(cudaMemcpy(d + 12 * n, st->p, 12 * n, cudaMemcpyDeviceToHost));
+    PM_CUDA_TRY(cudaMemcpy(d + 24 * n, st->id, 4 * n, cudaMemcpyDeviceToHost));
+    PM_CUDA_TRY(cudaMemcpy(d + 28 * n, st->f, 12 * n, cudaMemcpyDeviceToHost));
+  }
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return PM_EINVAL;
+  size_t w = std::fwrite(buf.data(), 1, buf.size(), fp);
+  int cl = std::fclose(fp);
+  return (w == buf.size() && cl == 0) ? PM_OK : PM_EINVAL;
+}
+
+int pm_state_load(pm_ctx* c, pm_state* st, const char* path) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!st || !path) return PM_EINVAL;
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return PM_EINVAL;
+  char hdr[kHeader + 1];
+  if (std::fread(hdr, 1, kHeader, fp) != kHeader) {
+    std::fclose(fp);
+    return PM_EINVAL;
+  }
+  hdr[kHeader] = 0;
+  long long n = -1;
+  double a = 0.0;
+  int fv = 0;
+  unsigned long long hash = 0;
+  const char* pf = std::strstr(hdr, "\"format\": \"pmnu-state-1\"");
+  const char* pn = std::strstr(hdr, "\"n\": ");
+  const char* pa = std::strstr(hdr, "\"a\": ");
+  const char* pv = std::strstr(hdr, "\"f_valid\": ");
+  const char* ph = std::strstr(hdr, "\"config_hash\": \"");
+  if (!pf || !pn || !pa || !pv || !ph || std::sscanf(pn + 5, "%lld", &n) != 1 ||
+      std::sscanf(pa + 5, "%lf", &a) != 1 || std::sscanf(pv + 11, "%d", &fv) != 1 ||
+      std::sscanf(ph + 16, "%16llx", &hash) != 1 || n != st->n || hash != config_hash(c->cfg)) {
+    std::fclose(fp);
+    return PM_EINVAL;
+  }
+  std::vector<char> buf((size_t)n * 40);
+  size_t r = std::fread(buf.data(), 1, buf.size(), fp);
+  std::fclose(fp);
+  if (r != buf.size()) return PM_EINVAL;
+  if (n > 0) {
+    if (!st->u || !st->p || !st->id || !st->f) return PM_EINVAL;
+    const char* d = buf.data();
+    PM_CUDA_TRY(cudaDeviceSynchronize());
+    PM_CUDA_TRY(cudaMemcpy(st->u, d, 12 * n, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(st->p, d + 12 * n, 12 * n, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(st->id, d + 24 * n, 4 * n, cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(st->f, d + 28 * n, 12 * n, cudaMemcpyHostToDevice));
+  }
+  st->a = a;
+  st->f_valid = fv;
+  return PM_OK;
 }
 
 int pm_fft_r2c(pm_ctx* c, const float* mesh, float* out_complex, void* stream) {

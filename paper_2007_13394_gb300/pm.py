@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_step_host": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, ctypes.POINTER(i32), d, d, d, vp]),
         "pm_power": (ctypes.c_int, [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
         "pm_ic": (ctypes.c_int, [vp, vp, d, d, ctypes.POINTER(State), vp]),
+        "pm_state_save": (ctypes.c_int, [vp, ctypes.POINTER(State), ctypes.c_char_p]),
+        "pm_state_load": (ctypes.c_int, [vp, ctypes.POINTER(State), ctypes.c_char_p]),
         "pm_fft_r2c": (ctypes.c_int, [vp, vp, vp, vp]),
         "pm_fft_c2r": (ctypes.c_int, [vp, vp, vp, vp]),
         "pm_potential": (ctypes.c_int, [vp, vp, vp, vp]),
@@ -291,6 +293,20 @@ class ParticleMesh:
                                    stream if stream is not None else _stream())
         _check(rc, "pm_step_host")
         return fv.value
+
+    def _state_struct(self, st):
+        return State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
+                     st["u"].shape[1], st.get("a", 0.0), int(st.get("f_valid", 0)), 0)
+
+    def save_state(self, st: dict, path: str):
+        s = self._state_struct(st)
+        _check(self.lib.pm_state_save(self.h, ctypes.byref(s), path.encode()), "pm_state_save")
+
+    def load_state(self, st: dict, path: str):
+        s = self._state_struct(st)
+        _check(self.lib.pm_state_load(self.h, ctypes.byref(s), path.encode()), "pm_state_load")
+        st["a"], st["f_valid"] = s.a, s.f_valid
+        return st
 
     def new_state(self, n):
         torch = _torch()

@@ -174,3 +174,33 @@ def test_full_size_benchmark_force_on_sampled_particles(pm):
     got = Fg[:, pick]
     rel = np.sqrt(((got - ref) ** 2).sum() / (ref ** 2).sum())
     assert rel < 1e-5, rel
+
+
+def test_checkpoint_resume_is_bit_identical(pm, tmp_path):
+    """Run 4 steps; or run 2, save, load into fresh arrays, run 2 more: identical state."""
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg1()
+    ctx = pm.ParticleMesh(cfg)
+    noise = torch.from_numpy(inputs.white_noise(cfg.nc, seed=6)).cuda()
+    sched = workloads.schedule_paper(25)
+    a = ctx.ic(noise, 0.01)
+    b = ctx.ic(noise, 0.01)
+    for s in sched[:4]:
+        ctx.step(a, *s)
+    for s in sched[:2]:
+        ctx.step(b, *s)
+    path = str(tmp_path / "state.pmnu")
+    ctx.save_state(b, path)
+    c = ctx.new_state(cfg.n_particles())
+    ctx.load_state(c, path)
+    assert c["a"] == b["a"] and c["f_valid"] == 1
+    for s in sched[2:4]:
+        ctx.step(c, *s)
+    ctx.sync()
+    for key in ("u", "p", "id", "f"):
+        assert torch.equal(a[key], c[key]), key
+    # a header for another configuration is refused
+    other = pm.ParticleMesh(workloads.cfg2_parity())
+    d = other.new_state(cfg.n_particles())
+    with pytest.raises(pm.PMError):
+        other.load_state(d, path)
