@@ -210,6 +210,38 @@ int pm_ic(pm_ctx* ctx, const float* noise, double a0, double k_fs, pm_state* st,
 int pm_state_save(pm_ctx* ctx, const pm_state* st, const char* path);
 int pm_state_load(pm_ctx* ctx, pm_state* st, const char* path);
 
+/* ---- adjoint (gradients of a final-field loss; no counterpart in the paper) ----- */
+
+/* Transpose of the paint with respect to the particle weights: out[i] = sum_c W(x_i - c)
+ * mesh(c) (the CIC readout; mesh N^3 contiguous).  Same as pm_readout. */
+int pm_paint_T(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* mesh, float* out, void* stream);
+/* Transpose of the readout: the deterministic CIC paint of signed per-particle weights
+ * w[n] (input order) onto mesh_out (N^3 contiguous). */
+int pm_readout_T(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* w, float* mesh_out,
+                 void* stream);
+/* VJP of the paint with respect to positions: grad[3n] (input order, Mpc/h^-1 units)
+ * = m_i grad_x sum_c W(x_i - c) lam_mesh(c), lam_mesh N^3 contiguous. */
+int pm_paint_vjp(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n,
+                 const float* lam_mesh, float* grad_out, void* stream);
+/* VJP of the PM force with respect to positions: grad[3n] = d <lam_f, F(x)> / dx, with
+ * F_j = R[G_j rho]: sum_j lam_f,j grad R[G_j rho] + m grad R[B], B = -sum_j G_j paint(lam_f,j)
+ * (G_j^T = -G_j: a real convolution with an odd kernel).  Arrays in input order. */
+int pm_force_vjp(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
+                 float* grad_out, void* stream);
+/* VJP of one KDK step a0 -> a1 (ah <= 0: arithmetic mean) at the checkpointed state st
+ * (u, p, id, f = F(x0) at a0, any order).  Cotangents lam_x1, lam_p1 of the state at a1
+ * and outputs lam_x0, lam_p0 are [3n] arrays indexed by canonical particle id.
+ * Positions are treated as continuous (units Mpc/h). */
+int pm_step_vjp(pm_ctx* ctx, const pm_state* st, double a0, double ah, double a1,
+                const float* lam_x1, const float* lam_p1, float* lam_x0, float* lam_p0,
+                void* stream);
+/* Transpose of the Zel'dovich initial conditions of pm_ic (same a0 and k_fs; pm_ic must
+ * have run on this context with that k_fs): cotangents of the initial positions and
+ * momenta (canonical order, [3n]) -> gradient with respect to the white noise
+ * (nc^3 contiguous). */
+int pm_ic_vjp(pm_ctx* ctx, const float* lam_x0, const float* lam_p0, double a0, double k_fs,
+              float* grad_noise, void* stream);
+
 /* ---- stage-level entry points (device arrays; for testing each kernel) ------- */
 
 /* Forward r2c FFT (unnormalised, e^{-ikx}) of a real N^3 mesh: out holds

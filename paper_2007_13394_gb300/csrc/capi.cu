@@ -111,6 +111,7 @@ void free_all(pm_ctx* c) {
   cudaFree(c->hs_p);
   cudaFree(c->hs_id);
   cudaFree(c->hs_f);
+  cudaFree(c->adj);
   for (auto& p : c->prof_live) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -689,6 +690,64 @@ int pm_readout(pm_ctx* c, const uint32_t* u, int64_t n, const float* mesh, float
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
 
+int pm_paint_T(pm_ctx* c, const uint32_t* u, int64_t n, const float* mesh, float* out, void* stream) {
+  return pm_readout(c, u, n, mesh, out, stream);
+}
+
+int pm_readout_T(pm_ctx* c, const uint32_t* u, int64_t n, const float* w, float* mesh_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || !mesh_out || (n > 0 && (!u || !w))) return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, nullptr, n, c->vals[0], s);
+  float* ws = c->ps;  // sorted weights in the momentum scratch
+  rc = gather_weights(c, w, n, ws, s);
+  if (rc != PM_OK) return rc;
+  paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, mesh_out, c->g.n, s, ws);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_paint_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_mesh,
+                 float* grad_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || (n > 0 && (!u || !lam_mesh || !grad_out))) return PM_EINVAL;
+  if (n == 0) return PM_OK;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
+  const float* m[1] = {lam_mesh};
+  readout_grad(c, n, m, 1, c->g.n, nullptr, c->vals[0], grad_out, false, s);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
+                 float* grad_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n < 0 || n > c->n_max || (n > 0 && (!u || !lam_f || !grad_out))) return PM_EINVAL;
+  return force_vjp(c, u, id, n, lam_f, grad_out, S(stream));
+}
+
+int pm_step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, const float* lam_x1,
+                const float* lam_p1, float* lam_x0, float* lam_p0, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  int rc = check_state(c, st);
+  if (rc != PM_OK) return rc;
+  if (!(a0 > 0.0) || !(a1 > a0) || a1 > 2.0) return PM_EINVAL;
+  if (ah <= 0.0) ah = 0.5 * (a0 + a1);
+  if (!(ah >= a0 && ah <= a1)) return PM_EINVAL;
+  if (st->n > 0 && (!lam_x1 || !lam_p1 || !lam_x0 || !lam_p0)) return PM_EINVAL;
+  return step_vjp(c, st, a0, ah, a1, lam_x1, lam_p1, lam_x0, lam_p0, S(stream));
+}
+
+int pm_ic_vjp(pm_ctx* c, const float* lam_x0, const float* lam_p0, double a0, double k_fs,
+              float* grad_noise, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!lam_x0 || !lam_p0 || !grad_noise || !(a0 > 0.0)) return PM_EINVAL;
+  return ic_vjp(c, lam_x0, lam_p0, a0, k_fs, grad_noise, S(stream));
+}
+
 int64_t pm_launch_count(pm_ctx* c) { return valid(c) ? c->launches : -1; }
 
 int pm_profile_enable(pm_ctx* c, int32_t mask) {
@@ -718,7 +777,7 @@ const char* pm_kernel_name(int32_t k) {
       "paint_tiles",   "fft_z_r2c",    "fft_y",        "fft_x_green",     "fft_x_grad",
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
       "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
-      "readout3_kick"};
+      "readout3_kick", "adjoint"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

@@ -38,7 +38,7 @@ constexpr int kAccWords = kTile * kSx;
 __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
-    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err) {
+    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts) {
   __shared__ long long acc[kAccWords];
   __shared__ uint32_t run_lo[14], run_pre[15];
   const int t = threadIdx.x;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     if (v < total) {
       while (v >= run_pre[r + 1]) ++r;  // v only grows, so the run index only grows
       const uint32_t k = run_lo[r] + (v - run_pre[r]);
-      m = id_mass(mt, ids[k], species, &bad);
+      m = wts ? wts[k] : id_mass(mt, ids[k], species, &bad);  // weights: signed, sorted order
       const uint32_t u0 = us[k], u1 = us[n + k], u2 = us[2 * n + k];
       int l[3] = {(int)(u0 >> shift) - ox, (int)(u1 >> shift) - oy, (int)(u2 >> shift) - oz};
 #pragma unroll
@@ -272,12 +272,12 @@ __global__ void k_repack_complex(const float2* __restrict__ src, int sp, float2*
 }  // namespace
 
 void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, int species,
-                 float* mesh, int row_pitch, cudaStream_t s) {
+                 float* mesh, int row_pitch, cudaStream_t s, const float* weights) {
   LaunchScope L(c, s, K_PAINT);
   unsigned grid = (unsigned)(c->nt * c->nt * c->nt);
   k_paint_tiles<<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species,
                                                c->g.n, 32 - c->g.logn, c->ntl, row_pitch,
-                                               c->err_dev);
+                                               c->err_dev, weights);
 }
 
 void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,

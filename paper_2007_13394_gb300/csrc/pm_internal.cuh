@@ -36,6 +36,7 @@ enum Kind {
   K_REPACK,
   K_FFT_X_FUSED,
   K_READOUT3_KICK,
+  K_ADJOINT,
   K_NUM_KINDS
 };
 
@@ -124,6 +125,9 @@ struct pm_ctx {
   uint32_t* hs_id = nullptr;
   float* hs_f = nullptr;
   int64_t hs_cap = 0;
+  // adjoint scratch: 8 x 3n floats (gathered cotangents, drifted positions, partial sums)
+  float* adj = nullptr;
+  int64_t adj_cap = 0;
   // instrumentation
   int64_t launches = 0;
   uint32_t prof = 0;  // bit k: time kernel kind k
@@ -154,8 +158,9 @@ int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s);                 // 
 void scan_exclusive(pm_ctx* c, const uint32_t* in, uint32_t* out, long long n, cudaStream_t s);
 void gather_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t* id, int64_t n,
                    const uint32_t* perm, cudaStream_t s);
+// weights (sorted order, signed) replace the species masses when non-null
 void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, int species,
-                 float* mesh, int row_pitch, cudaStream_t s);
+                 float* mesh, int row_pitch, cudaStream_t s, const float* weights = nullptr);
 void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, cudaStream_t s);
 void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* buf, int comp,
                            cudaStream_t s);
@@ -180,6 +185,17 @@ int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* 
               double* P_out, int64_t* nmodes_out, cudaStream_t s);
 int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s);
 float2* twiddles(pm_ctx* c, int n);
+// adjoint (k_adjoint.cu)
+void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes, int row_pitch,
+                  const float* wts_sorted, const uint32_t* perm, float* out, bool accumulate,
+                  cudaStream_t s);
+int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
+              float* grad, cudaStream_t s);
+int step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, const float* lx1,
+             const float* lp1, float* lx0, float* lp0, cudaStream_t s);
+int ic_vjp(pm_ctx* c, const float* lx, const float* lp, double a0, double k_fs, float* grad_noise,
+           cudaStream_t s);
+int gather_weights(pm_ctx* c, const float* w, int64_t n, float* w_sorted, cudaStream_t s);
 bool tma_init(pm_ctx* c);
 
 #define PM_CUDA_TRY(expr)                      \

@@ -84,6 +84,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_force_mesh": (ctypes.c_int, [vp, vp, i32, vp, vp]),
         "pm_readout": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "pm_power_bin_noalloc": (ctypes.c_int, [vp, vp, i32, d, i32, vp, vp, vp, vp]),
+        "pm_paint_T": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "pm_readout_T": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "pm_paint_vjp": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+        "pm_force_vjp": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+        "pm_step_vjp": (ctypes.c_int, [vp, ctypes.POINTER(State), d, d, d, vp, vp, vp, vp, vp]),
+        "pm_ic_vjp": (ctypes.c_int, [vp, vp, vp, d, d, vp, vp]),
         "pm_launch_count": (i64, [vp]),
         "pm_profile_enable": (ctypes.c_int, [vp, i32]),
         "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
@@ -363,6 +369,51 @@ class ParticleMesh:
         out = torch.empty(u.shape[1], dtype=torch.float32, device="cuda")
         _check(self.lib.pm_readout(self.h, _ptr(u), u.shape[1], _ptr(mesh), _ptr(out), _stream()), "pm_readout")
         return out
+
+    # ---- adjoint ----------------------------------------------------------------
+    def readout_T(self, u, w):
+        """Paint of signed per-particle weights (the readout's transpose)."""
+        torch = _torch()
+        mesh = torch.empty((self.n,) * 3, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_readout_T(self.h, _ptr(u), u.shape[1], _ptr(w), _ptr(mesh), _stream()), "pm_readout_T")
+        return mesh
+
+    def paint_T(self, u, mesh):
+        torch = _torch()
+        out = torch.empty(u.shape[1], dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_paint_T(self.h, _ptr(u), u.shape[1], _ptr(mesh), _ptr(out), _stream()), "pm_paint_T")
+        return out
+
+    def paint_vjp(self, u, ids, lam_mesh):
+        torch = _torch()
+        g = torch.empty((3, u.shape[1]), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_paint_vjp(self.h, _ptr(u), _ptr(ids), u.shape[1], _ptr(lam_mesh), _ptr(g), _stream()),
+               "pm_paint_vjp")
+        return g
+
+    def force_vjp(self, u, ids, lam_f):
+        torch = _torch()
+        g = torch.empty((3, u.shape[1]), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_force_vjp(self.h, _ptr(u), _ptr(ids), u.shape[1], _ptr(lam_f), _ptr(g), _stream()),
+               "pm_force_vjp")
+        return g
+
+    def step_vjp(self, st, a0, ah, a1, lam_x1, lam_p1):
+        """Cotangents (canonical id order) of the state after a step -> before it; st is the
+        checkpoint at a0 (u, p, id, f)."""
+        torch = _torch()
+        lx0 = torch.empty_like(lam_x1)
+        lp0 = torch.empty_like(lam_p1)
+        s = self._state_struct(st)
+        _check(self.lib.pm_step_vjp(self.h, ctypes.byref(s), a0, ah, a1, _ptr(lam_x1), _ptr(lam_p1), _ptr(lx0),
+                                    _ptr(lp0), _stream()), "pm_step_vjp")
+        return lx0, lp0
+
+    def ic_vjp(self, lam_x0, lam_p0, a0, k_fs=0.0):
+        torch = _torch()
+        g = torch.empty((self.cfg.nc,) * 3, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_ic_vjp(self.h, _ptr(lam_x0), _ptr(lam_p0), a0, k_fs, _ptr(g), _stream()), "pm_ic_vjp")
+        return g
 
     def launch_count(self):
         return int(self.lib.pm_launch_count(self.h))
