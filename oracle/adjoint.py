@@ -67,16 +67,17 @@ def paint_vjp_positions(u, mass, lam_mesh, n, box):
     return np.asarray(mass)[None, :] * readout_grad(u, lam_mesh, n, box)
 
 
-def force_vjp(u, mass, lam_f, n, box, omega_m0):
-    """d <lam_f, F(x)> / d x, shape (3, np)."""
-    phi = pm.potential_k(pm.paint(u, mass, n), box, omega_m0)
+def force_vjp(u, mass, lam_f, n, box, omega_m0, kfactor=None):
+    """d <lam_f, F(x)> / d x, shape (3, np).  kfactor: a real even multiplier of the
+    Green's function (the learned correction); G_j stays odd, so G_j^T = -G_j still."""
+    phi = pm.potential_k(pm.paint(u, mass, n), box, omega_m0, kfactor)
     out = np.zeros((3, u.shape[1]))
     for j in range(3):
         out += lam_f[j][None, :] * readout_grad(u, pm.force_mesh(phi, box, n, j), n, box)
     b = np.zeros((n, n, n))
     for j in range(3):
         a_j = pm.paint(u, lam_f[j], n)
-        b -= pm.force_mesh(pm.potential_k(a_j, box, omega_m0), box, n, j)
+        b -= pm.force_mesh(pm.potential_k(a_j, box, omega_m0, kfactor), box, n, j)
     return out + np.asarray(mass)[None, :] * readout_grad(u, b, n, box)
 
 

@@ -125,8 +125,12 @@ def cic_window(n):
     return np.sinc(nfull / n) ** 2, np.sinc(nhalf / n) ** 2      # np.sinc(x) = sin(pi x)/(pi x)
 
 
-def potential_k(mesh, box, omega_m0):
-    """phi_k = -(3/2) Omega_m0 FFT(rho/rho_bar) / N^3 / (k^2 W^2); phi_0 = 0."""
+def potential_k(mesh, box, omega_m0, kfactor=None):
+    """phi_k = -(3/2) Omega_m0 FFT(rho/rho_bar) / N^3 / (k^2 W^2); phi_0 = 0.
+
+    kfactor: optional real multiplier of the Green's function on the r2c half grid
+    (N, N, N/2 + 1), the learned correction m(|k|, a) of :mod:`oracle.mlp`.
+    """
     n = mesh.shape[0]
     dk = np.fft.rfftn(mesh)
     kfull, khalf, _, _ = wavenumbers(n, box)
@@ -136,6 +140,8 @@ def potential_k(mesh, box, omega_m0):
     with np.errstate(divide="ignore", invalid="ignore"):
         g = -1.5 * omega_m0 / n ** 3 / (k2 * w2)
     g[0, 0, 0] = 0.0
+    if kfactor is not None:
+        g = g * kfactor
     return dk * g
 
 
@@ -152,9 +158,9 @@ def force_mesh(phi_k, box, n, component):
     return np.fft.irfftn(fk, s=(n, n, n), axes=(0, 1, 2)) * n ** 3
 
 
-def force(u, mass, n, box, omega_m0):
-    """PM force (3, n_particles) at the particles."""
-    phi = potential_k(paint(u, mass, n), box, omega_m0)
+def force(u, mass, n, box, omega_m0, kfactor=None):
+    """PM force (3, n_particles) at the particles (kfactor: see :func:`potential_k`)."""
+    phi = potential_k(paint(u, mass, n), box, omega_m0, kfactor)
     return np.stack([readout(u, force_mesh(phi, box, n, j), n) for j in range(3)])
 
 
