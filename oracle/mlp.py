@@ -21,10 +21,11 @@ Readings (none of them is in the paper):
   (the int32 difference of the fixed-point positions times L / 2^32);
 * gradient: the FastPM step adjoint of :mod:`oracle.adjoint` plus, at every
   force evaluation F(x; a), the derivative with respect to the factor.  With
-  F_j = IFFT[h_j rho_k], h_j = -i k_j c(k) m(k), c the plain Green's function,
+  F_j = IFFT[h_j rho_k], h_j = -i D(k_j) c(k) m(k), c the plain Green's function
+  and D the gradient kernel of :mod:`oracle.pm`,
   and A_j = FFT(paint(lambda_F,j)):
       <lambda_F, F> = sum_j sum_k h_j(k) rho_k conj(A_j,k)   (full k grid),
-  so d<lambda_F, F>/dm(k) = Re sum_j (-i k_j) c(k) rho_k conj(A_j,k), counted
+  so d<lambda_F, F>/dm(k) = Re sum_j (-i D(k_j)) c(k) rho_k conj(A_j,k), counted
   twice for r2c modes with 0 < n_z < N/2, and the theta gradient is the
   network's backward pass weighted by it.
 """
@@ -117,24 +118,16 @@ def force(u, mass, n, box, omega_m0, theta, a):
     return pm.force(u, mass, n, box, omega_m0, factor_mesh(theta, n, a))
 
 
-def dloss_dfactor(u, mass, lam_f, n, box, omega_m0):
+def dloss_dfactor(u, mass, lam_f, n, box, omega_m0, kernel="fd4"):
     """d <lam_f, F> / d m(k) per r2c mode (with its r2c multiplicity), shape (N, N, N/2+1)."""
     rho_k = np.fft.rfftn(pm.paint(u, mass, n))
-    kfull, khalf, nfull, nhalf = pm.wavenumbers(n, box)
-    # plain Green's function c(k) on the half grid (the multiplier of delta_k in potential_k)
-    wfull, whalf = pm.cic_window(n)
-    k2 = kfull[:, None, None] ** 2 + kfull[None, :, None] ** 2 + khalf[None, None, :] ** 2
-    w2 = (wfull[:, None, None] * wfull[None, :, None] * whalf[None, None, :]) ** 2
-    with np.errstate(divide="ignore", invalid="ignore"):
-        cg = -1.5 * omega_m0 / n ** 3 / (k2 * w2)
-    cg[0, 0, 0] = 0.0
-    kx = np.where(nfull == -n // 2, 0.0, kfull)[:, None, None]
-    ky = np.where(nfull == -n // 2, 0.0, kfull)[None, :, None]
-    kz = np.where(nhalf == n // 2, 0.0, khalf)[None, None, :]
+    cg = pm.green_half(n, box, omega_m0, kernel)          # plain Green's function c(k)
+    dfull, dhalf = pm.gradient_kernel(n, box, kernel)
+    _, _, _, nhalf = pm.wavenumbers(n, box)
     q = np.zeros(rho_k.shape)
-    for j, kj in enumerate((kx, ky, kz)):
+    for j, dj in enumerate((dfull[:, None, None], dfull[None, :, None], dhalf[None, None, :])):
         a_j = np.fft.rfftn(pm.paint(u, lam_f[j], n))
-        q += np.real(-1j * kj * cg * rho_k * np.conj(a_j))
+        q += np.real(-1j * dj * cg * rho_k * np.conj(a_j))
     mult = np.where((nhalf > 0) & (nhalf < n // 2), 2.0, 1.0)[None, None, :]
     return q * mult
 
@@ -213,3 +206,12 @@ class LearnedRun:
             lam_x = lam_x + oad.force_vjp(u0, mass, lf0, n, box, om, m0)
             lam_p = lam_ph
         return L, g
+
+
+def adam_step(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2014, Algorithm 1): returns (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v

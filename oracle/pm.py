@@ -12,12 +12,18 @@ GPU path is held to:
 * cloud-in-cell (CIC) paint of rho / rho_bar: mass m at x gives
   m prod_d (1 - |x_d / H - i_d|) to the 8 nodes around it, periodic;
 * delta_k = FFT(rho / rho_bar) (forward e^{-ikx}, unnormalised); k = 0 dropped;
-* phi_k = -(3/2) Omega_m0 delta_k / N^3 / (k^2 W(k)^2) with
-  W(k) = prod_d sinc^2(k_d H / 2) (CIC window, deconvolved once for the paint
-  and once for the readout), k_d = 2 pi n_d / L, n_d in [-N/2, N/2);
-  Poisson source from §2.2 Eq. Om_pois (neutrinos count as matter);
-* F_j(x) = IFFT[-i k_j phi_k] (unnormalised inverse), with k_j = 0 at
-  n_j = -N/2 so the gradient stays odd and real;
+* phi_k = -(3/2) Omega_m0 delta_k / N^3 / k^2, k_d = 2 pi n_d / L,
+  n_d in [-N/2, N/2); Poisson source from §2.2 Eq. Om_pois (neutrinos count
+  as matter);
+* F_j(x) = IFFT[-i D(k_j) phi_k] (unnormalised inverse) with the 4-point
+  finite-difference gradient D(k) = (8 sin(kH) - sin(2kH)) / (6H), which is
+  real, odd and zero on the Nyquist index.  No CIC window deconvolution in the
+  force (the paper inherits FastPM's solver and names no kernel; this one
+  reproduces linear growth for a particle lattice coarser than the mesh, the
+  paper's mesh twice the CDM grid, and the Ewald force of an isolated particle,
+  where a spectral gradient with the W^-2 deconvolution does neither).  The
+  alternative kernel="spectral" is that deconvolved form: phi_k / W(k)^2 with
+  W(k) = prod_d sinc^2(k_d H / 2) and gradient k_j (0 at n_j = -N/2);
 * CIC readout of F_j at each particle with the paint's weights;
 * FastPM kick-drift-kick (§2.1 "Kick-Drift-Kick", §2.3) with the coefficients
   of :mod:`oracle.background`.
@@ -125,43 +131,70 @@ def cic_window(n):
     return np.sinc(nfull / n) ** 2, np.sinc(nhalf / n) ** 2      # np.sinc(x) = sin(pi x)/(pi x)
 
 
-def potential_k(mesh, box, omega_m0, kfactor=None):
-    """phi_k = -(3/2) Omega_m0 FFT(rho/rho_bar) / N^3 / (k^2 W^2); phi_0 = 0.
+KERNELS = ("fd4", "spectral")
+
+
+def gradient_kernel(n, box, kernel="fd4"):
+    """Per-axis gradient multiplier D(k) on the full axis and on the r2c half axis."""
+    kfull, khalf, nfull, nhalf = wavenumbers(n, box)
+    if kernel == "fd4":
+        H = box / n
+        d = lambda k: (8.0 * np.sin(k * H) - np.sin(2.0 * k * H)) / (6.0 * H)  # noqa: E731
+        dfull, dhalf = d(kfull), d(khalf)
+    elif kernel == "spectral":
+        dfull, dhalf = kfull.copy(), khalf.copy()
+    else:
+        raise ValueError(kernel)
+    dfull[nfull == -n // 2] = 0.0      # Nyquist index: zero (exactly, for the odd kernel)
+    dhalf[nhalf == n // 2] = 0.0
+    return dfull, dhalf
+
+
+def green_half(n, box, omega_m0, kernel="fd4"):
+    """Real multiplier c(k) of FFT(rho / rho_bar) giving phi_k on the r2c half grid; c(0) = 0."""
+    kfull, khalf, _, _ = wavenumbers(n, box)
+    k2 = kfull[:, None, None] ** 2 + kfull[None, :, None] ** 2 + khalf[None, None, :] ** 2
+    if kernel == "spectral":
+        wfull, whalf = cic_window(n)
+        k2 = k2 * (wfull[:, None, None] * wfull[None, :, None] * whalf[None, None, :]) ** 2
+    elif kernel != "fd4":
+        raise ValueError(kernel)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = -1.5 * omega_m0 / n ** 3 / k2
+    g[0, 0, 0] = 0.0
+    return g
+
+
+def potential_k(mesh, box, omega_m0, kfactor=None, kernel="fd4"):
+    """phi_k = c(k) FFT(rho/rho_bar), c = -(3/2) Omega_m0 / N^3 / k^2 (see green_half).
 
     kfactor: optional real multiplier of the Green's function on the r2c half grid
     (N, N, N/2 + 1), the learned correction m(|k|, a) of :mod:`oracle.mlp`.
     """
     n = mesh.shape[0]
-    dk = np.fft.rfftn(mesh)
-    kfull, khalf, _, _ = wavenumbers(n, box)
-    wfull, whalf = cic_window(n)
-    k2 = kfull[:, None, None] ** 2 + kfull[None, :, None] ** 2 + khalf[None, None, :] ** 2
-    w2 = (wfull[:, None, None] * wfull[None, :, None] * whalf[None, None, :]) ** 2
-    with np.errstate(divide="ignore", invalid="ignore"):
-        g = -1.5 * omega_m0 / n ** 3 / (k2 * w2)
-    g[0, 0, 0] = 0.0
+    g = green_half(n, box, omega_m0, kernel)
     if kfactor is not None:
         g = g * kfactor
-    return dk * g
+    return np.fft.rfftn(mesh) * g
 
 
-def force_mesh(phi_k, box, n, component):
-    """F_j(x) = IFFT_unnormalised[-i k_j phi_k] with k_j = 0 at the Nyquist index."""
-    kfull, khalf, nfull, nhalf = wavenumbers(n, box)
+def force_mesh(phi_k, box, n, component, kernel="fd4"):
+    """F_j(x) = IFFT_unnormalised[-i D(k_j) phi_k]."""
+    dfull, dhalf = gradient_kernel(n, box, kernel)
     if component == 0:
-        kj = np.where(nfull == -n // 2, 0.0, kfull)[:, None, None]
+        kj = dfull[:, None, None]
     elif component == 1:
-        kj = np.where(nfull == -n // 2, 0.0, kfull)[None, :, None]
+        kj = dfull[None, :, None]
     else:
-        kj = np.where(nhalf == n // 2, 0.0, khalf)[None, None, :]
+        kj = dhalf[None, None, :]
     fk = -1j * kj * phi_k
     return np.fft.irfftn(fk, s=(n, n, n), axes=(0, 1, 2)) * n ** 3
 
 
-def force(u, mass, n, box, omega_m0, kfactor=None):
+def force(u, mass, n, box, omega_m0, kfactor=None, kernel="fd4"):
     """PM force (3, n_particles) at the particles (kfactor: see :func:`potential_k`)."""
-    phi = potential_k(paint(u, mass, n), box, omega_m0, kfactor)
-    return np.stack([readout(u, force_mesh(phi, box, n, j), n) for j in range(3)])
+    phi = potential_k(paint(u, mass, n), box, omega_m0, kfactor, kernel)
+    return np.stack([readout(u, force_mesh(phi, box, n, j, kernel), n) for j in range(3)])
 
 
 # --------------------------------------------------------------- kick / drift
@@ -171,7 +204,7 @@ def drift(u, p, delta, box):
     return np.mod(np.asarray(u, dtype=np.float64) + step, TWO32).astype(np.uint64).astype(np.uint32)
 
 
-def kdk_step(u, p, f0, coeffs, mass, n, box, omega_m0):
+def kdk_step(u, p, f0, coeffs, mass, n, box, omega_m0, kernel="fd4"):
     """One FastPM KDK step with coefficients (K1, Delta, K2) and the force f0 at a0.
 
     Returns (u1, p1, f1) with f1 the force at a1 (the next step's first kick).
@@ -179,7 +212,7 @@ def kdk_step(u, p, f0, coeffs, mass, n, box, omega_m0):
     K1, delta, K2 = coeffs
     p = p + K1 * f0
     u = drift(u, p, delta, box)
-    f1 = force(u, mass, n, box, omega_m0)
+    f1 = force(u, mass, n, box, omega_m0, kernel=kernel)
     p = p + K2 * f1
     return u, p, f1
 
