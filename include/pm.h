@@ -19,10 +19,15 @@
  *               integer wraparound;
  *   paint       cloud-in-cell (CIC) of rho / rho_bar (mean 1) on an N^3 mesh,
  *               deterministic (tile-local integer accumulation, no float atomics);
- *   potential   phi_k = -(3/2) Omega_m0 delta_k / N^3 / (k^2 W(k)^2),
- *               W = prod_d sinc^2(pi n_d / N), phi_0 = 0;
- *   force       F_j = IFFT[-i k_j phi_k] with k_j = 0 on the Nyquist index,
- *               read out with the paint's CIC weights;
+ *   potential   phi_k = -(3/2) Omega_m0 delta_k / N^3 / k^2, phi_0 = 0;
+ *   force       F_j = IFFT[-i D(k_j) phi_k] with the 4-point finite-difference
+ *               gradient D(k) = (8 sin kH - sin 2kH) / (6H) (0 on the Nyquist
+ *               index), read out with the paint's CIC weights.  No window
+ *               deconvolution: with the mesh finer than the CDM lattice (the
+ *               paper's mesh is twice the CDM grid) a deconvolved spectral
+ *               kernel amplifies the lattice's alias modes and breaks linear
+ *               growth.  Flags bit 1 selects that kernel anyway
+ *               (phi_k / W(k)^2, W = prod_d sinc^2(pi n_d / N), gradient k_j);
  *   kick/drift  p += K F, u += rne(Delta p 2^32 / L) (int32 wraparound), with
  *               K1 = (g_p(a_h) - g_p(a_0)) / g_f(a_0),
  *               Delta = (D(a_1) - D(a_0)) / g_p(a_h),
@@ -75,6 +80,9 @@ enum {
 /* Species selectors for pm_paint and pm_power. */
 enum { PM_SPECIES_CDM = 1, PM_SPECIES_NU = 2, PM_SPECIES_ALL = 3 };
 
+/* pm_config.flags bits. */
+enum { PM_FLAG_TWO_MESH = 1, PM_FLAG_SPECTRAL_KERNEL = 2 };
+
 /* Run configuration.  Zero-initialise, then set the fields. */
 typedef struct pm_config {
   double box;          /* L, Mpc/h, > 0 */
@@ -94,8 +102,9 @@ typedef struct pm_config {
   int64_t n_max;       /* capacity of the sort scratch (>= every n passed later) */
   double ns;           /* spectral index of the synthetic initial spectrum (pm_ic) */
   double sigma8;       /* normalisation of the synthetic initial spectrum (pm_ic) */
-  uint32_t flags;      /* bit 0: two-mesh per-component force path (less memory; always used
-                          for nmesh = 2048); other bits 0 */
+  uint32_t flags;      /* bit 0 (PM_FLAG_TWO_MESH): two-mesh per-component force path (less
+                          memory; always used for nmesh = 2048); bit 1 (PM_FLAG_SPECTRAL_KERNEL):
+                          deconvolved spectral force kernel; other bits 0 */
   int32_t pad1;
 } pm_config;
 
@@ -241,6 +250,48 @@ int pm_step_vjp(pm_ctx* ctx, const pm_state* st, double a0, double ah, double a1
  * (nc^3 contiguous). */
 int pm_ic_vjp(pm_ctx* ctx, const float* lam_x0, const float* lam_p0, double a0, double k_fs,
               float* grad_noise, void* stream);
+
+/* ---- learned Green's-function correction (no counterpart in the paper) -------- */
+
+/* A small network m(kappa, a) = 1 + MLP(kappa, a) multiplies the Green's function of
+ * the potential: phi_k = -(3/2) Omega_m0 delta_k m(|k| / k_Ny, a) / N^3 / (k^2 W^2),
+ * k_Ny = pi N / L, a the scale factor of the force evaluation.  Network:
+ * Linear(2, 64) -> SiLU -> Linear(64, 64) -> SiLU -> Linear(64, 1); flat FP32
+ * parameters, in order W1[64][2] (row j: weights of kappa and a into unit j), b1[64],
+ * W2[64][64] (row = output unit), b2[64], w3[64], b3.  With w3 = b3 = 0 the kernel
+ * is the plain one exactly.  m depends on k through s = n_x^2 + n_y^2 + n_z^2 only
+ * and is evaluated once per s (table refreshed at every force evaluation). */
+enum { PM_MLP_HIDDEN = 64, PM_MLP_NPARAM = 4417 };
+
+/* Copies PM_MLP_NPARAM parameters from host memory and switches the factor on for
+ * every later force, potential, step and adjoint call; resets the Adam moments.
+ * theta == NULL switches it off.  Synchronous. */
+int pm_set_mlp(pm_ctx* ctx, const float* theta, int64_t nparam);
+/* Current parameters into host memory (after device work finishes).  Synchronous. */
+int pm_get_mlp(pm_ctx* ctx, float* theta, int64_t nparam);
+/* Scale factor at which pm_force, pm_potential and pm_force_vjp evaluate the factor
+ * (default 1); pm_step and pm_step_vjp use their own a0 and a1. */
+int pm_set_force_time(pm_ctx* ctx, double a);
+/* m at n points (device arrays kappa[n], a[n] -> m_out[n]). */
+int pm_mlp_eval(pm_ctx* ctx, const float* kappa, const float* a, int64_t n, float* m_out, void* stream);
+/* With the factor on, pm_force_vjp and pm_step_vjp also accumulate d L / d theta of
+ * the cotangents they are given (FP64 accumulator in the context; needs the
+ * three-mesh force path, PM_EINVAL otherwise).  This copies the accumulator to
+ * grad_out (device, nparam floats) and clears it when reset != 0. */
+int pm_mlp_grad(pm_ctx* ctx, float* grad_out, int64_t nparam, int32_t reset, void* stream);
+/* One Adam step (Kingma & Ba 2014) on the context's parameters with gradient grad
+ * (device), step count t >= 1 (bias corrections 1 - beta^t). */
+int pm_mlp_adam(pm_ctx* ctx, const float* grad, int64_t nparam, double lr, double beta1, double beta2,
+                double eps, int64_t t, void* stream);
+/* Training loss of the factor: L = sum_i m_i |x_i - y_i|^2 / sum_i m_i over the
+ * particles of the selected species (PM_SPECIES_*; the others weigh 0) of a state
+ * (u, id) of n particles and a reference run from the same initial conditions
+ * (u_ref, id_ref; either id may be NULL for canonical order), x - y the periodic
+ * difference int32(u - u_ref) L / 2^32.  lam_x[3n] (device, canonical order)
+ * receives dL/dx; *loss (host) receives L.  Ids must lie in [0, n).  Synchronous. */
+int pm_displacement_loss(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, const uint32_t* u_ref,
+                         const uint32_t* id_ref, int64_t n, int32_t species, float* lam_x, double* loss,
+                         void* stream);
 
 /* ---- stage-level entry points (device arrays; for testing each kernel) ------- */
 

@@ -12,7 +12,8 @@ chain rule of the forward oracle out step by step:
   the one-sided value of the cell the particle is in).
 * Force F_j(x_i) = R[G_j rho](x_i) with G_j the linear mesh operator of
   :func:`oracle.pm.force_mesh` o :func:`oracle.pm.potential_k`.  G_j is a real
-  convolution with an odd kernel (-i k_j times a real even Green's function), so
+  convolution with an odd kernel (-i D(k_j) times a real even Green's function,
+  D the gradient kernel of :mod:`oracle.pm`), so
   G_j^T = -G_j.  Hence for a cotangent lambda_F:
   dL/dx_i = sum_j lambda_F,ij grad R[G_j rho](x_i)
             + m_i grad R[B](x_i),  B = -sum_j G_j(paint(lambda_F,j)).

@@ -88,6 +88,7 @@ void free_all(pm_ctx* c) {
   for (auto& kv : c->tw) cudaFree(kv.second);
   cudaFree(c->ksq);
   cudaFree(c->winv);
+  cudaFree(c->wforce);
   cudaFree(c->kvec0);
   for (int i = 0; i < 2; ++i) {
     cudaFree(c->keys[i]);
@@ -112,6 +113,7 @@ void free_all(pm_ctx* c) {
   cudaFree(c->hs_id);
   cudaFree(c->hs_f);
   cudaFree(c->adj);
+  mlp_free(c);
   for (auto& p : c->prof_live) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -130,8 +132,9 @@ int sort_into_scratch(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
 // meshes and one readout reads them (per_all); without it, one component mesh at a
 // time in meshA (per_comp).
 template <class F1, class F3>
-int force_components(pm_ctx* c, int64_t n, cudaStream_t s, F1&& per_comp, F3&& per_all) {
+int force_components(pm_ctx* c, int64_t n, double a, cudaStream_t s, F1&& per_comp, F3&& per_all) {
   float* realA = reinterpret_cast<float*>(c->meshA);
+  mlp_table(c, a, s);
   paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, 2 * c->g.pc, s);
   if (c->meshC) {
     fft_force_fused(c, c->g, c->meshA, c->meshB, c->meshC, s);
@@ -168,7 +171,7 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
     if (rc != PM_OK) return rc;
     gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
     force_components(
-        c, n, s,
+        c, n, a0, s,
         [&](int comp, float* mesh) {
           readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, st->p, st->f,
                        comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
@@ -186,7 +189,7 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
   gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
   // force at a1 and the second half kick, written back in tile order
   force_components(
-      c, n, s,
+      c, n, a1, s,
       [&](int comp, float* mesh) {
         readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, (float)k[2], st->p, st->f,
                      comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
@@ -336,10 +339,10 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
   }
   // flag bit 0, or a 2048^3 mesh: per-component force path with two meshes (at 2048^3 it is
   // also the faster one: reading three 34 GB meshes at once starves the readout)
-  const bool two_mesh = (cfg->flags & 1u) != 0 || N >= 2048;
+  const bool two_mesh = (cfg->flags & PM_FLAG_TWO_MESH) != 0 || N >= 2048;
   if ((!two_mesh && dalloc(&c->meshC, me)) || dalloc(&c->meshA, me) || dalloc(&c->meshB, me) ||
       dalloc(&c->ksq, N) ||
-      dalloc(&c->winv, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
+      dalloc(&c->winv, N) || dalloc(&c->wforce, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
       dalloc(&c->keys[1], nm) || dalloc(&c->vals[0], nm) || dalloc(&c->vals[1], nm) ||
       dalloc(&c->us, 3 * nm) || dalloc(&c->ps, 3 * nm) || dalloc(&c->ids, nm) ||
       dalloc(&c->counts, c->nbuckets + 1) || dalloc(&c->bstart, c->nbuckets + 1) ||
@@ -356,21 +359,29 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
     return PM_ENOMEM;
   }
   cudaMemset(c->err_dev, 0, sizeof(int));
-  // k tables of the force mesh (FP64 on the host, stored as float)
+  // k tables of the force mesh (FP64 on the host, stored as float).  Force kernel:
+  // phi_k = -1.5 Omega_m0 delta_k / N^3 / k^2 and the 4-point finite-difference gradient
+  // D(k) = (8 sin kH - sin 2kH) / (6H); flags bit 1 selects the deconvolved spectral form
+  // (phi_k / W(k)^2, gradient k).  D is 0 on the Nyquist index either way.
   {
-    std::vector<float> ksq(N), winv(N), kv(N);
-    const double kF = 2.0 * 3.14159265358979323846 / cfg->box;
+    const bool spectral = (cfg->flags & PM_FLAG_SPECTRAL_KERNEL) != 0;
+    std::vector<float> ksq(N), winv(N), wf(N), kv(N);
+    const double pi = 3.14159265358979323846;
+    const double kF = 2.0 * pi / cfg->box, H = cfg->box / N;
     for (int i = 0; i < N; ++i) {
       int ns = i < N / 2 ? i : i - N;
       double k = kF * ns;
-      double x = 3.14159265358979323846 * ns / N;
+      double x = pi * ns / N;
       double sinc = ns == 0 ? 1.0 : std::sin(x) / x;
       ksq[i] = (float)(k * k);
       winv[i] = (float)(1.0 / std::pow(sinc, 4));
-      kv[i] = (i == N / 2) ? 0.0f : (float)k;
+      wf[i] = spectral ? winv[i] : 1.0f;
+      const double d = spectral ? k : (8.0 * std::sin(k * H) - std::sin(2.0 * k * H)) / (6.0 * H);
+      kv[i] = (i == N / 2) ? 0.0f : (float)d;
     }
     cudaMemcpy(c->ksq, ksq.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     cudaMemcpy(c->winv, winv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->wforce, wf.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
     cudaMemcpy(c->kvec0, kv.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
   }
   tma_init(c);  // tensor maps for the TMA strided passes (classic kernels if unavailable)
@@ -459,7 +470,7 @@ int pm_force(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, float*
   if (rc != PM_OK) return rc;
   gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
   force_components(
-      c, n, s,
+      c, n, c->force_a, s,
       [&](int comp, float* mesh) {
         readout_kick(c, c->us, nullptr, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, nullptr, F_out,
                      nullptr, nullptr, c->vals[0], s);
@@ -662,6 +673,7 @@ int pm_potential(pm_ctx* c, const float* mesh, float* out_complex, void* stream)
   if (!mesh || !out_complex) return PM_EINVAL;
   cudaStream_t s = S(stream);
   repack_real(c, c->g, mesh, c->g.n, reinterpret_cast<float*>(c->meshA), 2 * c->g.pc, s);
+  mlp_table(c, c->force_a, s);
   fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
   repack_complex(c, c->g, c->meshB, c->g.pc, reinterpret_cast<float2*>(out_complex),
                  c->g.n / 2 + 1, s);
@@ -726,7 +738,7 @@ int pm_force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, co
                  float* grad_out, void* stream) {
   if (!valid(c)) return PM_ENOTINIT;
   if (n < 0 || n > c->n_max || (n > 0 && (!u || !lam_f || !grad_out))) return PM_EINVAL;
-  return force_vjp(c, u, id, n, lam_f, grad_out, S(stream));
+  return force_vjp(c, u, id, n, lam_f, c->force_a, grad_out, S(stream));
 }
 
 int pm_step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, const float* lam_x1,
@@ -777,7 +789,7 @@ const char* pm_kernel_name(int32_t k) {
       "paint_tiles",   "fft_z_r2c",    "fft_y",        "fft_x_green",     "fft_x_grad",
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
       "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
-      "readout3_kick", "adjoint"};
+      "readout3_kick", "adjoint",      "mlp_table",    "mlp_backward", "mlp_misc"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

@@ -148,10 +148,18 @@ __device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, i
 // Fused epilogue / prologue of the x pass.
 struct KTables {
   const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)
-  const float* winv;   // 1 / sinc^4(pi n_s / N)
-  const float* kvec0;  // k_n with the Nyquist index set to 0
+  const float* winv;   // per-axis factor of the Green's function (1, or 1 / sinc^4(pi n_s / N))
+  const float* kvec0;  // gradient kernel D(k_n), 0 on the Nyquist index
   float gcoef;         // -1.5 Omega_m0 / N^3
+  const float* mtab;   // learned factor by |n|^2 (n signed indices), null: plain kernel
 };
+
+// |n|^2 of a half-spectrum mode from its unsigned indices (kz <= M/2 is its own |n_z|)
+template <int M>
+__device__ __forceinline__ int nsq_index(int kx, int ky, int kz) {
+  const int nx = kx < M / 2 ? kx : kx - M, ny = ky < M / 2 ? ky : ky - M;
+  return nx * nx + ny * ny + kz * kz;
+}
 
 enum { EPI_NONE = 0, EPI_GREEN = 1 };
 enum { PRO_NONE = 0, PRO_GRAD = 1 };

@@ -7,7 +7,7 @@
 // * Force VJP for a cotangent lambda_F (F_j = R[G_j rho], G_j real with an odd
 //   kernel so G_j^T = -G_j):
 //     dL/dx_i = sum_j lambda_F,ij grad R[G_j rho](x_i) + m_i grad R[B](x_i),
-//     B_k = sum_j i k_j g(k) FFT(paint(lambda_F,j))_k.
+//     B_k = sum_j i D(k_j) g(k) FFT(paint(lambda_F,j))_k, D the gradient kernel.
 // * KDK step VJP (p_h = p0 + K1 F(x0), x1 = x0 + Delta p_h, p1 = p_h + K2 F(x1)).
 // * Zel'dovich IC transpose: s_j = T_j omega with T_j = IFFT diag(S_j) FFT, so
 //   dL/domega = IFFT(sum_j conj(S_j) FFT(lambda_s,j)), neutrino sites with the
@@ -79,19 +79,32 @@ __global__ void k_readout_grad(const uint32_t* __restrict__ us, const uint32_t* 
   }
 }
 
-// B_k (+)= i k_j g(k) A_k on the half spectrum (padded pitch pc), the transpose of -G_j.
+// B_k (+)= i D(k_j) g(k) m(k) A_k on the half spectrum (padded pitch pc), the transpose
+// of -G_j (D the gradient kernel); m = 1 without the learned factor.  With rho (the
+// density's half spectrum) it also bins d <lambda_F, F> / d m(k) =
+// Re[(-i D(k_j)) g rho_k conj(A_k)] (twice for 0 < k_z < N/2) by s = |n|^2 into gbin.
 __global__ void k_adj_combine(const float2* __restrict__ a, float2* __restrict__ b, int nm, int pc,
                               const float* __restrict__ ksq, const float* __restrict__ winv,
-                              const float* __restrict__ kvec0, float gcoef, int comp, int accumulate) {
+                              const float* __restrict__ kvec0, float gcoef, int comp, int accumulate,
+                              const float* __restrict__ mtab, const float2* __restrict__ rho,
+                              double* __restrict__ gbin) {
   const int x = blockIdx.x / nm, y = blockIdx.x % nm;
+  const int nx = x < nm / 2 ? x : x - nm, ny = y < nm / 2 ? y : y - nm;
   for (int kz = threadIdx.x; kz <= nm / 2; kz += blockDim.x) {
     const size_t idx = ((size_t)x * nm + y) * pc + kz;
+    const int sidx = nx * nx + ny * ny + kz * kz;
     const float k2 = ksq[x] + ksq[y] + ksq[kz];
     float g = gcoef * winv[x] * winv[y] * winv[kz] / k2;
     if (k2 == 0.0f) g = 0.0f;
     const float kj = comp == 0 ? kvec0[x] : (comp == 1 ? kvec0[y] : kvec0[kz]);
-    const float s = kj * g;
     const float2 v = a[idx];
+    if (rho) {
+      const float2 r = rho[idx];
+      const float mult = (kz > 0 && kz < nm / 2) ? 2.0f : 1.0f;
+      const float q = mult * kj * g * (r.y * v.x - r.x * v.y);
+      if (q != 0.0f) atomicAdd(gbin + sidx, (double)q);
+    }
+    const float s = kj * (mtab ? g * mtab[sidx] : g);
     const float2 r = make_float2(-s * v.y, s * v.x);  // i s v
     if (accumulate) {
       float2 o = b[idx];
@@ -244,9 +257,13 @@ void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes,
 }
 
 // Force VJP: u (any order, with id), cotangent lam_f[3n] in the same order -> grad[3n].
+// With the learned factor (evaluated at scale factor a) it also accumulates
+// d <lam_f, F> / d theta; that needs the third mesh, which holds rho_k meanwhile.
 int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
-              float* grad, cudaStream_t s) {
+              double a, float* grad, cudaStream_t s) {
   if (n == 0) return PM_OK;
+  const bool learned = c->mlp_on;
+  if (learned && !c->meshC) return PM_EINVAL;
   int rc = ensure_adj(c, n);
   if (rc != PM_OK) return rc;
   rc = sort_particles(c, u, n, s);
@@ -262,25 +279,33 @@ int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const
   const int rp = 2 * c->g.pc;
   // term 1: sum_j lambda_j grad R[G_j rho]
   paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s);
-  fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
+  if (learned) {
+    mlp_table(c, a, s);
+    fft_forward(c, c->g, c->meshA, c->meshC, 0, s);  // rho_k, kept for the factor's gradient
+    mlp_green_apply(c, c->meshC, c->meshB, s);
+  } else {
+    fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
+  }
   for (int j = 0; j < 3; ++j) {
     fft_inverse_component(c, c->g, c->meshB, c->meshA, j, s);
     const float* m[1] = {realA};
     readout_grad(c, n, m, 1, rp, lam_s + (int64_t)j * n, c->vals[0], grad, j > 0, s);
   }
-  // term 2: m_i grad R[B], B_k = sum_j i k_j g FFT(paint(lambda_j))
+  // term 2: m_i grad R[B], B_k = sum_j i D(k_j) g FFT(paint(lambda_j))
   const double nn = (double)c->g.n;
   const float gcoef = (float)(-1.5 * c->cosmo.omega_m0 / (nn * nn * nn));
   for (int j = 0; j < 3; ++j) {
     paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s, lam_s + (int64_t)j * n);
     fft_forward(c, c->g, c->meshA, c->meshA, 0, s);
     LaunchScope L(c, s, K_ADJOINT);
-    k_adj_combine<<<(unsigned)(c->g.n * c->g.n), 128, 0, s>>>(c->meshA, c->meshB, c->g.n, c->g.pc, c->ksq,
-                                                            c->winv, c->kvec0, gcoef, j, j > 0);
+    k_adj_combine<<<(unsigned)(c->g.n * c->g.n), 128, 0, s>>>(
+        c->meshA, c->meshB, c->g.n, c->g.pc, c->ksq, c->wforce, c->kvec0, gcoef, j, j > 0,
+        learned ? c->mlp_tab : nullptr, learned ? c->meshC : nullptr, c->mlp_gbin);
   }
   fft_inverse_plain(c, c->g, c->meshB, s);
   const float* m[1] = {realB};
   readout_grad(c, n, m, 1, rp, nullptr, c->vals[0], grad, true, s);
+  if (learned) mlp_backward(c, a, s);
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
 
@@ -309,14 +334,14 @@ int step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, con
                                               (float)(k[1] * 4294967296.0 / c->cfg.box), u1)));
   // lambda_x1' = lambda_x1 + F_vjp(x1; K2 lambda_p1)
   ADJ((k_by_id<<<blocks(n), 256, 0, s>>>(Lp, lamF, nullptr, n, 0, (float)k[2])));
-  rc = force_vjp(c, u1, st->id, n, lamF, g, s);
+  rc = force_vjp(c, u1, st->id, n, lamF, a1, g, s);
   if (rc != PM_OK) return rc;
   ADJ((k_axpby<<<blocks(m3), 256, 0, s>>>(g, Lx, m3, 1.0f, 1.0f)));
   // lambda_ph = lambda_p1 + Delta lambda_x1'
   ADJ((k_axpby<<<blocks(m3), 256, 0, s>>>(Lx, Lp, m3, (float)k[1], 1.0f)));
   // lambda_x0 = lambda_x1' + F_vjp(x0; K1 lambda_ph)
   ADJ((k_by_id<<<blocks(n), 256, 0, s>>>(Lp, lamF, nullptr, n, 0, (float)k[0])));
-  rc = force_vjp(c, st->u, st->id, n, lamF, g, s);
+  rc = force_vjp(c, st->u, st->id, n, lamF, a0, g, s);
   if (rc != PM_OK) return rc;
   ADJ((k_axpby<<<blocks(m3), 256, 0, s>>>(g, Lx, m3, 1.0f, 1.0f)));
   ADJ((k_by_id<<<blocks(n), 256, 0, s>>>(Lx, lx0, st->id, n, 1, 1.0f)));

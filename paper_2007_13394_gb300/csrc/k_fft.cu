@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
       const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
       float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
       if (k2 == 0.0f) g = 0.0f;
+      if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
       v[s] = cscale(v[s], g);
     }
   }
@@ -180,6 +181,7 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
       const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
       float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
       if (k2 == 0.0f) g = 0.0f;
+      if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
       v[s] = cscale(v[s], g);
       phis[(j + s * Q) * TK + c] = v[s];                   // read back by this thread only
       const float kk = __ldg(kt.kvec0 + kx);
@@ -308,10 +310,11 @@ void strided(pm_ctx* c, const Geom& g, const float2* src, float2* dst, int axis,
 KTables ktables(pm_ctx* c, const Geom& g) {
   KTables kt;
   kt.ksq = c->ksq;
-  kt.winv = c->winv;
+  kt.winv = c->wforce;
   kt.kvec0 = c->kvec0;
   double nn = (double)g.n;
   kt.gcoef = (float)(-1.5 * c->cosmo.omega_m0 / (nn * nn * nn));
+  kt.mtab = (c->mlp_on && g.n == c->g.n) ? c->mlp_tab : nullptr;
   return kt;
 }
 

@@ -162,6 +162,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
         const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
         float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
         if (k2 == 0.0f) g = 0.0f;
+        if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
         v[s] = cscale(v[s], g);
         if constexpr (MODE == MODE_FUSED) {
           in[(j + s * Q) * TK + c] = v[s];               // phi, read back by this thread only

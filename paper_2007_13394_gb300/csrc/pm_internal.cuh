@@ -37,6 +37,9 @@ enum Kind {
   K_FFT_X_FUSED,
   K_READOUT3_KICK,
   K_ADJOINT,
+  K_MLP_TABLE,
+  K_MLP_BACKWARD,
+  K_MLP_MISC,
   K_NUM_KINDS
 };
 
@@ -86,10 +89,14 @@ struct pm_ctx {
   // tensor maps of meshA/B/C for the TMA strided passes: [mesh][0: x-pass box, 1: y-pass box]
   CUtensorMap tmap[3][2];
   bool tma_ok = false;
-  // per-size tables: twiddles e^{-2 pi i t / n} (n entries), |k|^2, 1/sinc^4, k with Nyquist 0
+  // per-size tables: twiddles e^{-2 pi i t / n} (n entries); per force-mesh index: |k|^2,
+  // 1/sinc^4 (the power spectrum's window compensation), the force Green's function's
+  // per-axis factor (1, or 1/sinc^4 for the deconvolved spectral kernel) and the
+  // gradient kernel D(k) (4-point finite difference, or k; 0 on the Nyquist index)
   std::map<int, float2*> tw;
   float* ksq = nullptr;
   float* winv = nullptr;
+  float* wforce = nullptr;
   float* kvec0 = nullptr;
   // sort / particle scratch
   uint32_t* keys[2] = {nullptr, nullptr};
@@ -128,6 +135,16 @@ struct pm_ctx {
   // adjoint scratch: 8 x 3n floats (gathered cotangents, drifted positions, partial sums)
   float* adj = nullptr;
   int64_t adj_cap = 0;
+  // learned Green's-function factor m(|k| / k_Ny, a) = 1 + MLP (null theta: plain kernel)
+  bool mlp_on = false;
+  float* mlp_theta = nullptr;     // PM_MLP_NPARAM parameters
+  float* mlp_tab = nullptr;       // m at |n|^2 = s for s in [0, mlp_ntab), refreshed per force
+  int64_t mlp_ntab = 0;           // 3 (N/2)^2 + 1
+  double* mlp_gbin = nullptr;     // d <lambda_F, F> / d m per s (adjoint, then cleared)
+  double* mlp_dtheta = nullptr;   // accumulated d L / d theta
+  float* mlp_adam = nullptr;      // Adam first and second moments, 2 x PM_MLP_NPARAM
+  double* mlp_red = nullptr;      // device scalars of the displacement loss reductions
+  double force_a = 1.0;           // scale factor of pm_force / pm_potential / pm_force_vjp
   // instrumentation
   int64_t launches = 0;
   uint32_t prof = 0;  // bit k: time kernel kind k
@@ -190,13 +207,22 @@ void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes,
                   const float* wts_sorted, const uint32_t* perm, float* out, bool accumulate,
                   cudaStream_t s);
 int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
-              float* grad, cudaStream_t s);
+              double a, float* grad, cudaStream_t s);
 int step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, const float* lx1,
              const float* lp1, float* lx0, float* lp0, cudaStream_t s);
 int ic_vjp(pm_ctx* c, const float* lx, const float* lp, double a0, double k_fs, float* grad_noise,
            cudaStream_t s);
 int gather_weights(pm_ctx* c, const float* w, int64_t n, float* w_sorted, cudaStream_t s);
 bool tma_init(pm_ctx* c);
+// learned factor (k_mlp.cu)
+int mlp_set(pm_ctx* c, const float* theta_host, int64_t nparam);
+void mlp_free(pm_ctx* c);
+// refreshes the |n|^2 table for scale factor a when the learned factor is on
+void mlp_table(pm_ctx* c, double a, cudaStream_t s);
+// phi_k = c(k) m(k) rho_k on the force mesh's half spectrum (src and dst padded)
+void mlp_green_apply(pm_ctx* c, const float2* rho_k, float2* phi_k, cudaStream_t s);
+// d L / d theta += backward of the network over mlp_gbin at scale factor a; clears mlp_gbin
+void mlp_backward(pm_ctx* c, double a, cudaStream_t s);
 
 #define PM_CUDA_TRY(expr)                      \
   do {                                         \

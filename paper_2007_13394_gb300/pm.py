@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpmnu.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
 SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
+MLP_HIDDEN, MLP_NPARAM = 64, 4417
 
 
 class PMError(RuntimeError):
@@ -90,6 +91,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_force_vjp": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "pm_step_vjp": (ctypes.c_int, [vp, ctypes.POINTER(State), d, d, d, vp, vp, vp, vp, vp]),
         "pm_ic_vjp": (ctypes.c_int, [vp, vp, vp, d, d, vp, vp]),
+        "pm_set_mlp": (ctypes.c_int, [vp, vp, i64]),
+        "pm_get_mlp": (ctypes.c_int, [vp, vp, i64]),
+        "pm_set_force_time": (ctypes.c_int, [vp, d]),
+        "pm_mlp_eval": (ctypes.c_int, [vp, vp, vp, i64, vp, vp]),
+        "pm_mlp_grad": (ctypes.c_int, [vp, vp, i64, i32, vp]),
+        "pm_mlp_adam": (ctypes.c_int, [vp, vp, i64, d, d, d, d, i64, vp]),
+        "pm_displacement_loss": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i32, vp, dp, vp]),
         "pm_launch_count": (i64, [vp]),
         "pm_profile_enable": (ctypes.c_int, [vp, i32]),
         "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
@@ -414,6 +422,53 @@ class ParticleMesh:
         g = torch.empty((self.cfg.nc,) * 3, dtype=torch.float32, device="cuda")
         _check(self.lib.pm_ic_vjp(self.h, _ptr(lam_x0), _ptr(lam_p0), a0, k_fs, _ptr(g), _stream()), "pm_ic_vjp")
         return g
+
+    # ---- learned Green's-function factor ---------------------------------------
+    def set_mlp(self, theta):
+        """Switch the learned factor on with host parameters (MLP_NPARAM floats); None: off."""
+        if theta is None:
+            _check(self.lib.pm_set_mlp(self.h, None, 0), "pm_set_mlp")
+            return
+        t = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        _check(self.lib.pm_set_mlp(self.h, t.ctypes.data_as(ctypes.c_void_p), t.size), "pm_set_mlp")
+
+    def get_mlp(self):
+        t = np.zeros(MLP_NPARAM, dtype=np.float32)
+        _check(self.lib.pm_get_mlp(self.h, t.ctypes.data_as(ctypes.c_void_p), t.size), "pm_get_mlp")
+        return t
+
+    def set_force_time(self, a):
+        _check(self.lib.pm_set_force_time(self.h, a), "pm_set_force_time")
+
+    def mlp_eval(self, kappa, a):
+        torch = _torch()
+        out = torch.empty_like(kappa)
+        _check(self.lib.pm_mlp_eval(self.h, _ptr(kappa), _ptr(a), kappa.numel(), _ptr(out), _stream()),
+               "pm_mlp_eval")
+        return out
+
+    def mlp_grad(self, reset=True):
+        torch = _torch()
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_mlp_grad(self.h, _ptr(g), MLP_NPARAM, 1 if reset else 0, _stream()), "pm_mlp_grad")
+        return g
+
+    def mlp_adam(self, grad, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(self.lib.pm_mlp_adam(self.h, _ptr(grad), MLP_NPARAM, lr, beta1, beta2, eps, int(t), _stream()),
+               "pm_mlp_adam")
+
+    def displacement_loss(self, st, ref, species=SPECIES_ALL):
+        """(L, dL/dx in canonical order) of a state against a reference state (same ICs),
+        over the particles of the selected species."""
+        torch = _torch()
+        n = st["u"].shape[1]
+        lam = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        out = ctypes.c_double()
+        _check(self.lib.pm_displacement_loss(self.h, _ptr(st["u"]), _ptr(st["id"]), _ptr(ref["u"]),
+                                             _ptr(ref.get("id")), n, species, _ptr(lam), ctypes.byref(out),
+                                             _stream()),
+               "pm_displacement_loss")
+        return out.value, lam
 
     def launch_count(self):
         return int(self.lib.pm_launch_count(self.h))

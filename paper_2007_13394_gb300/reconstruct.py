@@ -18,6 +18,7 @@ class FinalDensity(torch.autograd.Function):
     @staticmethod
     def forward(ctx, noise, pmctx: ParticleMesh, steps, a0: float, k_fs: float):
         st = pmctx.ic(noise.contiguous(), a0, k_fs=k_fs)
+        pmctx.set_force_time(a0)
         st["f"].copy_(pmctx.force(st["u"], st["id"]))
         st["f_valid"] = 1
         ckpts = []

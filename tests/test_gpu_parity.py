@@ -203,7 +203,8 @@ def test_readout_matches_oracle(pm):
 
 
 # ------------------------------------------------------------------ force
-@pytest.mark.parametrize("flags", [0, 1], ids=["fused_x", "per_component"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3], ids=["fused_x", "per_component", "fused_x_spectral",
+                                                     "per_component_spectral"])
 @pytest.mark.parametrize("size", ["cfg1", "cfg2_parity"])
 def test_force_relative_rms_below_1e5(pm, size, flags):
     if size == "cfg1":
@@ -215,7 +216,8 @@ def test_force_relative_rms_below_1e5(pm, size, flags):
     ctx = pm.ParticleMesh(cfg)
     F = ctx.force(pm.as_u32_tensor(o["u"])).cpu().numpy().astype(np.float64)
     ctx.sync()
-    ref = opm.force(o["u"], o["mass"], cfg.nmesh, cfg.box, o["bg"].omega_m0)
+    ref = opm.force(o["u"], o["mass"], cfg.nmesh, cfg.box, o["bg"].omega_m0,
+                    kernel="spectral" if flags & 2 else "fd4")
     rel = np.sqrt(((F - ref) ** 2).sum() / (ref ** 2).sum())
     assert rel < 1e-5, rel
 
