@@ -215,3 +215,48 @@ def adam_step(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     mhat = m / (1.0 - beta1 ** t)
     vhat = v / (1.0 - beta2 ** t)
     return theta - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# ------------------------------------------------------------- spectrum loss
+def power_vjp(u, mass, n, box, nbins, dL_dP):
+    """d L / d x (3, n_particles) for L depending on the binned auto-spectrum of the painted
+    mass (:func:`oracle.pm.power_spectrum` of paint(u, mass)) through dL_dP[b].
+
+    With F = FFT(rho), rho_bar its mean, P_b = (V / N^6) sum_{k in b} |F_k|^2 /
+    (rho_bar^2 W_k^2) / N_b over the full grid (N_b its mode count) and rho_bar fixed by
+    the total mass: dL/drho(x) = 2 sum_k c_k F_k e^{ikx}, c_k = dL/dP_b V / (N^6 rho_bar^2
+    W_k^2 N_b) for k in bin b; then the paint's position VJP.
+    """
+    mass = np.broadcast_to(np.asarray(mass, dtype=np.float64), (u.shape[1],))
+    rho = pm.paint(u, mass, n)
+    F = np.fft.rfftn(rho)
+    rho_bar = rho.mean()
+    kfull, khalf, nfull, nhalf = pm.wavenumbers(n, box)
+    kmag = np.sqrt(kfull[:, None, None] ** 2 + kfull[None, :, None] ** 2 + khalf[None, None, :] ** 2)
+    kf = 2.0 * np.pi / box
+    b = np.floor((kmag - 0.5 * kf) / kf).astype(np.int64)
+    ok = (kmag >= 0.5 * kf) & (b < nbins)
+    mult = np.where((nhalf > 0) & (nhalf < n // 2), 2.0, 1.0)[None, None, :] * np.ones_like(kmag)
+    counts = np.bincount(b[ok], weights=mult[ok], minlength=nbins)
+    wfull, whalf = pm.cic_window(n)
+    w2 = (wfull[:, None, None] * wfull[None, :, None] * whalf[None, None, :]) ** 2
+    g = np.asarray(dL_dP, dtype=np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        per_bin = np.where(counts > 0, g / counts, 0.0)
+    c = np.zeros(F.shape)
+    c[ok] = per_bin[b[ok]]
+    c = c * box ** 3 / (float(n) ** 6 * rho_bar ** 2 * w2)
+    lam = 2.0 * n ** 3 * np.fft.irfftn(c * F, s=(n, n, n), axes=(0, 1, 2))
+    return oad.paint_vjp_positions(u, mass, lam, n, box)
+
+
+def power_loss(u, mass, n, box, nbins, p_ref, bins):
+    """Spectrum-matching loss L = mean_{b in bins} (P_b / P_ref,b - 1)^2 of the total
+    painted mass and dL/dP (length nbins, zero outside bins)."""
+    _, P, _ = pm.power_spectrum(pm.paint(u, mass, n), None, box, nbins)
+    sel = np.zeros(nbins, dtype=bool)
+    sel[list(bins)] = True
+    r = P[sel] / np.asarray(p_ref)[sel] - 1.0
+    g = np.zeros(nbins)
+    g[sel] = 2.0 * r / (sel.sum() * np.asarray(p_ref)[sel])
+    return float(np.mean(r ** 2)), g
