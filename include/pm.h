@@ -232,6 +232,13 @@ int pm_readout_T(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* w, floa
  * = m_i grad_x sum_c W(x_i - c) lam_mesh(c), lam_mesh N^3 contiguous. */
 int pm_paint_vjp(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n,
                  const float* lam_mesh, float* grad_out, void* stream);
+/* VJP of pm_power's auto-spectrum (species_a = species_b = species) with respect to the
+ * positions: grad_out[3n] (device, input order) = sum_b dL_dP[b] dP_b / dx, dL_dP a host
+ * array of nbins.  dP_b/drho(x) = 2 sum_{k in b} V F_k e^{ikx} / (N^6 rho_bar^2 W_k^2 N_b)
+ * (F = FFT of the species mesh, rho_bar its mean, fixed by the species' total mass),
+ * then the paint's position VJP.  Synchronous. */
+int pm_power_vjp(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species,
+                 int32_t nbins, const double* dL_dP, float* grad_out, void* stream);
 /* VJP of the PM force with respect to positions: grad[3n] = d <lam_f, F(x)> / dx, with
  * F_j = R[G_j rho]: sum_j lam_f,j grad R[G_j rho] + m grad R[B], B = -sum_j G_j paint(lam_f,j)
  * (G_j^T = -G_j: a real convolution with an odd kernel).  Arrays in input order. */

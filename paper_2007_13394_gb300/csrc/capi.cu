@@ -104,6 +104,7 @@ void free_all(pm_ctx* c) {
   cudaFree(c->scan_tmp);
   cudaFree(c->pk_partial);
   cudaFree(c->pk_final);
+  cudaFree(c->pk_w);
   cudaFree(c->ic_amp);
   cudaFree(c->ic_amp_nu);
   cudaFree(c->err_dev);
@@ -732,6 +733,26 @@ int pm_paint_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, co
   const float* m[1] = {lam_mesh};
   readout_grad(c, n, m, 1, c->g.n, nullptr, c->vals[0], grad_out, false, s);
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_power_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species,
+                 int32_t nbins, const double* dL_dP, float* grad_out, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (n <= 0 || n > c->n_max || !u || !dL_dP || !grad_out || species < 1 || species > 3 || nbins < 1)
+    return PM_EINVAL;
+  cudaStream_t s = S(stream);
+  int rc = sort_into_scratch(c, u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
+  float* realA = reinterpret_cast<float*>(c->meshA);
+  paint_tiles(c, c->us, c->ids, n, species, realA, 2 * c->g.pc, s);
+  fft_forward(c, c->g, c->meshA, c->meshA, 0, s);
+  rc = power_weight(c, nbins, dL_dP, s);
+  if (rc != PM_OK) return rc;
+  fft_inverse_plain(c, c->g, c->meshA, s);
+  const float* m[1] = {realA};
+  readout_grad(c, n, m, 1, 2 * c->g.pc, nullptr, c->vals[0], grad_out, false, s, species);
+  return pm_sync(c, stream);
 }
 
 int pm_force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,

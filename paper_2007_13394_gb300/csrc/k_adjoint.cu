@@ -32,7 +32,7 @@ __global__ void k_readout_grad(const uint32_t* __restrict__ us, const uint32_t* 
                                const float* __restrict__ m2, int nmesh_used, int nm, int shift,
                                int row_pitch, float inv_h, const float* __restrict__ wts, MassTable mt,
                                const uint32_t* __restrict__ perm, float* __restrict__ out,
-                               int accumulate) {
+                               int accumulate, int species) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t ux = us[i], uy = us[n + i], uz = us[2 * n + i];
@@ -47,7 +47,7 @@ __global__ void k_readout_grad(const uint32_t* __restrict__ us, const uint32_t* 
   const size_t r10 = ((size_t)cx1 * nm + cy) * row_pitch, r11 = ((size_t)cx1 * nm + cy1) * row_pitch;
   const float* ms[3] = {m0, m1, m2};
   bool bad = false;
-  const float mass = wts ? 0.0f : id_mass(mt, ids[i], PM_SPECIES_ALL, &bad);
+  const float mass = wts ? 0.0f : id_mass(mt, ids[i], species, &bad);
   float o[3] = {0.f, 0.f, 0.f};
   for (int j = 0; j < nmesh_used; ++j) {
     const float* M = ms[j];
@@ -246,14 +246,14 @@ int gather_weights(pm_ctx* c, const float* w, int64_t n, float* w_sorted, cudaSt
 // Readout gradient of up to three padded meshes at the sorted scratch particles
 void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes, int row_pitch,
                   const float* wts_sorted, const uint32_t* perm, float* out, bool accumulate,
-                  cudaStream_t s) {
+                  cudaStream_t s, int species) {
   if (n == 0) return;
   LaunchScope L(c, s, K_ADJOINT);
   const float inv_h = (float)(c->g.n / c->cfg.box);
   k_readout_grad<<<blocks(n), 256, 0, s>>>(c->us, c->ids, n, meshes[0], nmeshes > 1 ? meshes[1] : nullptr,
                                            nmeshes > 2 ? meshes[2] : nullptr, nmeshes, c->g.n,
                                            32 - c->g.logn, row_pitch, inv_h, wts_sorted, c->mt, perm,
-                                           out, accumulate ? 1 : 0);
+                                           out, accumulate ? 1 : 0, species);
 }
 
 // Force VJP: u (any order, with id), cotangent lam_f[3n] in the same order -> grad[3n].

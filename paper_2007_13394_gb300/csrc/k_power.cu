@@ -9,6 +9,8 @@
 // partials in plane order.
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "pm_internal.cuh"
 
 namespace pmnu {
@@ -73,7 +75,58 @@ __global__ void k_power_reduce(const double* __restrict__ partial, int nplanes, 
   out[i] = s;
 }
 
+// d *= cw[b(n)] / W(k)^2 on the half spectrum (0 at k = 0 and beyond the last bin): the
+// k-space cotangent of a binned auto-spectrum (the factor 2 and V / (N^6 rho_bar^2 N_b)
+// folded into cw on the host).
+__global__ void k_power_weight(float2* __restrict__ d, int nm, int pc, int nbins,
+                               const float* __restrict__ winv, const float* __restrict__ cw) {
+  const int x = blockIdx.x;
+  const int nx = x < nm / 2 ? x : x - nm;
+  const int nzc = nm / 2 + 1;
+  const float wx = __ldg(winv + x);
+  for (int q = threadIdx.x; q < nm * nzc; q += blockDim.x) {
+    const int y = q / nzc, kz = q % nzc;
+    const int ny = y < nm / 2 ? y : y - nm;
+    const long long n2 = (long long)nx * nx + (long long)ny * ny + (long long)kz * kz;
+    const size_t idx = ((size_t)x * nm + y) * pc + kz;
+    float w = 0.0f;
+    if (n2 > 0) {
+      const int b = bin_of(n2);
+      if (b < nbins) w = __ldg(cw + b) * wx * __ldg(winv + y) * __ldg(winv + kz);
+    }
+    d[idx] = cscale(d[idx], w);
+  }
+}
+
 }  // namespace
+
+// Cotangent mesh of sum_b dL_dP[b] P_b (auto-spectrum of the half spectrum in meshA, in
+// place): meshA <- c_k F_k, c_k = 2 dL_dP[b] V / (N^6 rho_bar^2 W_k^2 N_b).  Synchronous
+// (the mode counts N_b and rho_bar come from the binning pass).
+int power_weight(pm_ctx* c, int nbins, const double* dL_dP, cudaStream_t s) {
+  if (nbins < 1 || nbins > kMaxBins) return PM_EINVAL;
+  std::vector<double> kb(nbins), Pb(nbins);
+  std::vector<int64_t> nb(nbins);
+  float2 f0;
+  PM_CUDA_TRY(cudaMemcpyAsync(&f0, c->meshA, sizeof(float2), cudaMemcpyDeviceToHost, s));
+  int rc = power_bin(c, c->meshA, c->meshA, nbins, kb.data(), Pb.data(), nb.data(), s);
+  if (rc != PM_OK) return rc;
+  const Geom& g = c->g;
+  const double nn = (double)g.n, n3 = nn * nn * nn;
+  const double rho_bar = (double)f0.x / n3;
+  std::vector<float> cw(nbins, 0.0f);
+  if (rho_bar != 0.0) {
+    const double V = c->cfg.box * c->cfg.box * c->cfg.box;
+    for (int b = 0; b < nbins; ++b)
+      if (nb[b] > 0) cw[b] = (float)(2.0 * dL_dP[b] * V / (n3 * n3 * rho_bar * rho_bar * (double)nb[b]));
+  }
+  if (!c->pk_w && cudaMalloc(&c->pk_w, sizeof(float) * kMaxBins) != cudaSuccess) return PM_ENOMEM;
+  PM_CUDA_TRY(cudaMemcpyAsync(c->pk_w, cw.data(), sizeof(float) * nbins, cudaMemcpyHostToDevice, s));
+  LaunchScope L(c, s, K_POWER_BIN);
+  k_power_weight<<<g.n, kPowThreads, 0, s>>>(c->meshA, g.n, g.pc, nbins, c->winv, c->pk_w);
+  PM_CUDA_TRY(cudaStreamSynchronize(s));  // cw lives on this stack frame until the copy ends
+  return PM_OK;
+}
 
 int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* k_out,
               double* P_out, int64_t* nmodes_out, cudaStream_t s) {

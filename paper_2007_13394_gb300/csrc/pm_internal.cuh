@@ -118,6 +118,7 @@ struct pm_ctx {
   // power binning partials
   double* pk_partial = nullptr;
   double* pk_final = nullptr;
+  float* pk_w = nullptr;        // per-bin weights of the spectrum VJP
   // initial-condition tables
   float* ic_amp = nullptr;      // sqrt(P/V) nc^1.5 by integer |n|^2, CDM and filtered neutrino
   float* ic_amp_nu = nullptr;
@@ -200,12 +201,13 @@ void repack_complex(pm_ctx* c, const Geom& g, const float2* src, int src_pitch, 
                     int dst_pitch, cudaStream_t s);
 int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* k_out,
               double* P_out, int64_t* nmodes_out, cudaStream_t s);
+int power_weight(pm_ctx* c, int nbins, const double* dL_dP, cudaStream_t s);
 int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s);
 float2* twiddles(pm_ctx* c, int n);
 // adjoint (k_adjoint.cu)
 void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes, int row_pitch,
                   const float* wts_sorted, const uint32_t* perm, float* out, bool accumulate,
-                  cudaStream_t s);
+                  cudaStream_t s, int species = PM_SPECIES_ALL);
 int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const float* lam_f,
               double a, float* grad, cudaStream_t s);
 int step_vjp(pm_ctx* c, const pm_state* st, double a0, double ah, double a1, const float* lx1,

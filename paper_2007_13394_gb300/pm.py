@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_readout_T": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "pm_paint_vjp": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
         "pm_force_vjp": (ctypes.c_int, [vp, vp, vp, i64, vp, vp, vp]),
+        "pm_power_vjp": (ctypes.c_int, [vp, vp, vp, i64, i32, i32, vp, vp, vp]),
         "pm_step_vjp": (ctypes.c_int, [vp, ctypes.POINTER(State), d, d, d, vp, vp, vp, vp, vp]),
         "pm_ic_vjp": (ctypes.c_int, [vp, vp, vp, d, d, vp, vp]),
         "pm_set_mlp": (ctypes.c_int, [vp, vp, i64]),
@@ -397,6 +398,15 @@ class ParticleMesh:
         g = torch.empty((3, u.shape[1]), dtype=torch.float32, device="cuda")
         _check(self.lib.pm_paint_vjp(self.h, _ptr(u), _ptr(ids), u.shape[1], _ptr(lam_mesh), _ptr(g), _stream()),
                "pm_paint_vjp")
+        return g
+
+    def power_vjp(self, u, ids, dL_dP, species=SPECIES_ALL):
+        """d L / d x (input order) for L depending on the binned auto-spectrum through dL_dP."""
+        torch = _torch()
+        w = np.ascontiguousarray(np.asarray(dL_dP, dtype=np.float64))
+        g = torch.empty((3, u.shape[1]), dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_power_vjp(self.h, _ptr(u), _ptr(ids), u.shape[1], species, w.size,
+                                     w.ctypes.data_as(ctypes.c_void_p), _ptr(g), _stream()), "pm_power_vjp")
         return g
 
     def force_vjp(self, u, ids, lam_f):

@@ -167,3 +167,18 @@ def test_training_gradient_matches_oracle(pm):
     L_ref, g_ref = run.grad(noise.astype(np.float64), th.astype(np.float64), target)
     assert L == pytest.approx(L_ref, rel=1e-3)
     assert _rel(g, g_ref) < 2e-3
+
+
+def test_power_vjp_matches_oracle(pm):
+    cfg = _cfg(pm)
+    ctx = pm.ParticleMesh(cfg)
+    rec = oad.Reconstruction(cfg, [], 0.1)
+    u, _ = rec.ics(inputs.white_noise(cfg.nc, seed=20).astype(np.float64) * 30.0)
+    nb = 20
+    dL_dP = inputs.normal_values(nb, seed=21)
+    rng = np.random.default_rng(22)
+    order = rng.permutation(u.shape[1]).astype(np.uint32)         # input order != canonical
+    g = ctx.power_vjp(pm.as_u32_tensor(np.ascontiguousarray(u[:, order])), pm.as_u32_tensor(order), dL_dP)
+    ctx.sync()
+    ref = om.power_vjp(u, rec.mass, cfg.nmesh, cfg.box, nb, dL_dP)[:, order]
+    assert _rel(g.double().cpu().numpy(), ref) < 1e-4
