@@ -6,10 +6,19 @@
 // high face layer (class bits) also reaches the neighbouring tile, which reads
 // exactly those classes of its seven low-side neighbours.  Each (particle,
 // corner) pair is therefore counted by the one CTA that owns the corner cell.
-// Contributions are accumulated in shared memory as 64-bit fixed point
-// (2^-32 resolution): integer addition is associative, so the result does not
-// depend on thread scheduling, and no global float atomics are used.
+// Contributions are accumulated in shared memory as fixed-point integers: integer
+// addition is associative, so the result does not depend on thread scheduling, and
+// no float atomics are used.  Mass paints use 2^-24 resolution, each contribution
+// q split as q = hi 2^12 + lo (0 <= lo < 2^12) into two 32-bit accumulators (32-bit
+// shared atomics run ~4x faster than 64-bit ones, and 32-bit conversions avoid the
+// narrow FP64 pipe that 64-bit float <-> integer conversions use); a tile whose
+// particle count could overflow them (count >= 2^17 or count x max mass >= 2^19),
+// masses of 128 or more, and the signed weights of the adjoint use one 64-bit
+// accumulator instead (resolution 2^-24 for masses, so both forms give the same
+// bits; 2^-32 for weights).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "pm_internal.cuh"
 
@@ -19,8 +28,11 @@ namespace {
 
 constexpr int kPaintThreads = 256;
 constexpr int kTileCells = kTile * kTile * kTile;  // 4096
-constexpr float kFix = 4294967296.0f;              // 2^32
-constexpr float kUnfix = 2.3283064365386963e-10f;  // 2^-32
+constexpr float kFixW = 4294967296.0f;              // 2^32: signed weights
+constexpr float kUnfixW = 2.3283064365386963e-10f;  // 2^-32
+constexpr float kFixM = 16777216.0f;                // 2^24: masses
+constexpr float kUnfixM = 5.9604644775390625e-08f;  // 2^-24
+constexpr int kLoBits = 12;
 
 // The 14 bucket runs a tile reads, as (neighbour offset o, first class, end class):
 // its own tile (all classes), then for each low-side neighbour o the classes that
@@ -38,8 +50,12 @@ constexpr int kAccWords = kTile * kSx;
 __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
-    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts) {
+    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts,
+    float mmax) {
+  // one 64-bit accumulator, or the same bytes as two 32-bit halves (hi words, then lo words)
   __shared__ long long acc[kAccWords];
+  unsigned int* const acc_hi = reinterpret_cast<unsigned int*>(acc);
+  unsigned int* const acc_lo = acc_hi + kAccWords;
   __shared__ uint32_t run_lo[14], run_pre[15];
   const int t = threadIdx.x;
   for (int i = t; i < kAccWords; i += kPaintThreads) acc[i] = 0;
@@ -72,54 +88,49 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   const float fscale = 1.0f / (float)(1u << shift);
   const uint32_t fmask = (1u << shift) - 1u;
   const uint32_t total = run_pre[14];
-  // A warp takes 32 particles per round, one per lane (coalesced loads), then paints them
-  // in 8 sub-rounds of 4: lane = 8 * (particle slot) + corner (bx, by, bz), the particle's
-  // data broadcast by shuffles.  A particle's 8 corners hit 8 distinct bank pairs.
-  const int lane = t & 31, warp = t >> 5;
-  const int bx = (lane >> 2) & 1, by = (lane >> 1) & 1, bz = lane & 1;
-  const int corner_off = bx * kSx + by * kSy + bz;
+  // One particle per thread (coalesced loads in bucket order), its 8 corners added by
+  // the same thread.
+  // split: 32-bit accumulators and 32-bit conversions (GB300's FP64 pipe, which runs
+  // the 64-bit float <-> integer conversions, is narrow); w 2^24 < 2^31 needs mmax < 128
+  const bool split = wts == nullptr && mmax < 128.0f && total < (1u << 17) && (float)total * mmax < 524288.0f;
+  const float fix = wts ? kFixW : kFixM;
   const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
   bool bad = false;
   int r = 0;
-  for (uint32_t base = warp * 32; base < total; base += kPaintThreads) {
-    const uint32_t v = base + lane;
-    int cell = -1;                    // packed local cell (x * kSx + y * kSy + z) of the lower corner
-    float fx = 0.f, fy = 0.f, fz = 0.f, m = 0.f;
-    int lo_ok = 0;                    // bit d: lower corner inside along d; bit 3 + d: upper inside
-    if (v < total) {
-      while (v >= run_pre[r + 1]) ++r;  // v only grows, so the run index only grows
-      const uint32_t k = run_lo[r] + (v - run_pre[r]);
-      m = wts ? wts[k] : id_mass(mt, ids[k], species, &bad);  // weights: signed, sorted order
-      const uint32_t u0 = us[k], u1 = us[n + k], u2 = us[2 * n + k];
-      int l[3] = {(int)(u0 >> shift) - ox, (int)(u1 >> shift) - oy, (int)(u2 >> shift) - oz};
+  for (uint32_t v = t; v < total; v += kPaintThreads) {
+    while (v >= run_pre[r + 1]) ++r;  // v only grows, so the run index only grows
+    const uint32_t k = run_lo[r] + (v - run_pre[r]);
+    const float m = wts ? wts[k] : id_mass(mt, ids[k], species, &bad);  // weights: signed, sorted order
+    if (m == 0.0f) continue;
+    const uint32_t u0 = us[k], u1 = us[n + k], u2 = us[2 * n + k];
+    int l[3] = {(int)(u0 >> shift) - ox, (int)(u1 >> shift) - oy, (int)(u2 >> shift) - oz};
+    int lo_ok = 0;  // bit d: lower corner inside along d; bit 3 + d: upper inside
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {  // periodic wrap relative to the tile origin
-        if (l[d] > nm / 2) l[d] -= nm;
-        if (l[d] < -nm / 2) l[d] += nm;
-        if (l[d] >= 0 && l[d] < kTile) lo_ok |= 1 << d;
-        if (l[d] + 1 >= 0 && l[d] + 1 < kTile) lo_ok |= 8 << d;
-      }
-      cell = l[0] * kSx + l[1] * kSy + l[2];
-      fx = (float)(u0 & fmask) * fscale;
-      fy = (float)(u1 & fmask) * fscale;
-      fz = (float)(u2 & fmask) * fscale;
+    for (int d = 0; d < 3; ++d) {  // periodic wrap relative to the tile origin
+      if (l[d] > nm / 2) l[d] -= nm;
+      if (l[d] < -nm / 2) l[d] += nm;
+      if (l[d] >= 0 && l[d] < kTile) lo_ok |= 1 << d;
+      if (l[d] + 1 >= 0 && l[d] + 1 < kTile) lo_ok |= 8 << d;
     }
+    const int cell = l[0] * kSx + l[1] * kSy + l[2];
+    const float fx = (float)(u0 & fmask) * fscale, fy = (float)(u1 & fmask) * fscale,
+                fz = (float)(u2 & fmask) * fscale;
 #pragma unroll
-    for (int sub = 0; sub < 8; ++sub) {
-      const int src = sub * 4 + (lane >> 3);
-      const int c_s = __shfl_sync(0xffffffffu, cell, src);
-      const int ok_s = __shfl_sync(0xffffffffu, lo_ok, src);
-      const float fx_s = __shfl_sync(0xffffffffu, fx, src);
-      const float fy_s = __shfl_sync(0xffffffffu, fy, src);
-      const float fz_s = __shfl_sync(0xffffffffu, fz, src);
-      const float m_s = __shfl_sync(0xffffffffu, m, src);
-      const bool inside = ((ok_s >> (bx ? 3 : 0)) & 1) && ((ok_s >> (by ? 4 : 1)) & 1) &&
-                          ((ok_s >> (bz ? 5 : 2)) & 1);
-      if (m_s != 0.0f && inside) {
-        const float w =
-            (bx ? fx_s : 1.0f - fx_s) * (by ? fy_s : 1.0f - fy_s) * (bz ? fz_s : 1.0f - fz_s) * m_s;
-        const long long q = __float2ll_rn(w * kFix);
-        atomicAdd((unsigned long long*)&acc[c_s + corner_off], (unsigned long long)q);
+    for (int corner = 0; corner < 8; ++corner) {
+      const int bx = corner >> 2, by = (corner >> 1) & 1, bz = corner & 1;
+      const bool inside = ((lo_ok >> (bx ? 3 : 0)) & 1) && ((lo_ok >> (by ? 4 : 1)) & 1) &&
+                          ((lo_ok >> (bz ? 5 : 2)) & 1);
+      if (inside) {
+        const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz) * m;
+        const int ad = cell + bx * kSx + by * kSy + bz;
+        if (split) {
+          const unsigned int q = __float2uint_rn(w * fix);  // < 2^31: masses below 128
+          atomicAdd(&acc_hi[ad], q >> kLoBits);
+          atomicAdd(&acc_lo[ad], q & ((1u << kLoBits) - 1u));
+        } else {
+          const long long q = __float2ll_rn(w * fix);
+          atomicAdd((unsigned long long*)&acc[ad], (unsigned long long)q);
+        }
       }
     }
   }
@@ -129,9 +140,23 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   for (int q = t; q < kTile * kTile * kTile / 4; q += kPaintThreads) {
     int row = q >> 2, z4 = (q & 3) * 4;
     int lx = row >> 4, ly = row & 15;
-    const long long* a = &acc[lx * kSx + ly * kSy + z4];
-    float4 v = make_float4(__ll2float_rn(a[0]) * kUnfix, __ll2float_rn(a[1]) * kUnfix,
-                           __ll2float_rn(a[2]) * kUnfix, __ll2float_rn(a[3]) * kUnfix);
+    const int a0 = lx * kSx + ly * kSy + z4;
+    float fv[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (split) {
+        // value = hi 2^12 + lo; for hi, lo < 2^24 both terms are exact floats, so one
+        // correctly rounded addition equals the rounded conversion of the 64-bit sum
+        const unsigned int hi = acc_hi[a0 + e], lo = acc_lo[a0 + e];
+        fv[e] = (hi < (1u << 24) && lo < (1u << 24))
+                    ? __fadd_rn(__uint2float_rn(hi) * (float)(1 << kLoBits), __uint2float_rn(lo))
+                    : __ll2float_rn(((long long)hi << kLoBits) + (long long)lo);
+      } else {
+        fv[e] = __ll2float_rn(acc[a0 + e]);
+      }
+    }
+    const float un = wts ? kUnfixW : kUnfixM;
+    float4 v = make_float4(fv[0] * un, fv[1] * un, fv[2] * un, fv[3] * un);
     size_t off = ((size_t)(ox + lx) * nm + (oy + ly)) * (size_t)row_pitch + oz + z4;
     *reinterpret_cast<float4*>(mesh + off) = v;
   }
@@ -241,9 +266,12 @@ __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ 
     for (int d = 0; d < 3; ++d) {
       float pv = p[d * n + i] + K1 * f[d * n + i];
       p[d * n + i] = pv;
-      // u += rne(Delta p 2^32 / L), modulo 2^32
-      long long step = __float2ll_rn(dscale * pv);
-      uu[d] = u[d * n + i] + (uint32_t)(unsigned long long)step;
+      // u += rne(Delta p 2^32 / L), modulo 2^32; the 32-bit conversion (same rounding)
+      // whenever the step fits, the 64-bit one (FP64 pipe) only for steps of 2^31 or more
+      const float x = dscale * pv;
+      const uint32_t step = fabsf(x) < 2147483648.0f ? (uint32_t)__float2int_rn(x)
+                                                     : (uint32_t)(unsigned long long)__float2ll_rn(x);
+      uu[d] = u[d * n + i] + step;
       u[d * n + i] = uu[d];
     }
     key = tile_key(uu[0], uu[1], uu[2], shift, ntl);
@@ -275,9 +303,13 @@ void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, 
                  float* mesh, int row_pitch, cudaStream_t s, const float* weights) {
   LaunchScope L(c, s, K_PAINT);
   unsigned grid = (unsigned)(c->nt * c->nt * c->nt);
+  float mmax = 0.0f;  // largest particle mass of the painted species
+  if (species & PM_SPECIES_CDM) mmax = std::max(mmax, c->mt.m_cdm);
+  if (species & PM_SPECIES_NU)
+    for (int i = 0; i < c->mt.nshell && i < kMaxShell; ++i) mmax = std::max(mmax, c->mt.m_nu[i]);
   k_paint_tiles<<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species,
                                                c->g.n, 32 - c->g.logn, c->ntl, row_pitch,
-                                               c->err_dev, weights);
+                                               c->err_dev, weights, mmax);
 }
 
 void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,

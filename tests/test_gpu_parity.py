@@ -144,6 +144,30 @@ def test_paint_uniform_random_and_empty(pm):
     assert not empty.any()
 
 
+def test_paint_clustered_tiles(pm):
+    """Most particles in a few cells and on tile faces: tiles far above one chunk of the
+    paint's per-tile staging, columns with thousands of particles, halo classes."""
+    cfg = make_cfg(pm, nmesh=128, n_max=300000)
+    ctx = pm.ParticleMesh(cfg)
+    rng = np.random.default_rng(12)
+    n = 300000
+    u = inputs.uniform_positions(n, seed=13)
+    cells = rng.integers(0, 8, size=(3, 2 * n // 3)) * 16 + rng.integers(14, 16, size=(3, 2 * n // 3))
+    u[:, : 2 * n // 3] = (cells.astype(np.uint64) * (2 ** 32 // 128)
+                          + rng.integers(0, 2 ** 25, size=(3, 2 * n // 3))).astype(np.uint32)
+    ids = np.arange(n, dtype=np.uint32) % cfg.n_cdm()
+    m = ctx.paint(pm.as_u32_tensor(u), pm.as_u32_tensor(ids)).cpu().numpy()
+    m2 = ctx.paint(pm.as_u32_tensor(u), pm.as_u32_tensor(ids)).cpu().numpy()
+    ctx.sync()
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    _, _, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+    mc, _ = onu.species_masses(128, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
+                               bg.omega_nu_poisson, m_shell)
+    ref = opm.paint(u, np.full(n, mc), 128)
+    assert np.array_equal(m, m2)
+    np.testing.assert_allclose(m, ref, rtol=2e-6, atol=2e-6 * ref.max())
+
+
 def test_paint_rejects_unknown_ids(pm):
     cfg = make_cfg(pm)
     ctx = pm.ParticleMesh(cfg)
