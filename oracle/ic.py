@@ -148,3 +148,27 @@ def neutrino_particles(noise, box, pk, D0, gp0, n_sites, n_shell, n_fib, q_shell
     x = np.broadcast_to(x, (3, nsite, n_shell, ndir)).reshape(3, -1)
     p = np.broadcast_to(p, (3, nsite, n_shell, ndir)).reshape(3, -1)
     return pm.quantise(x, box), p
+
+
+def pseudo_neutrino_particles(noise, box, pk, D0, gp0, n_sites, uniforms, masses_ev, p_scale, k_fs=0.0):
+    """Pseudo-random neutrino sampling (the comparison scheme of §3 Fig. Pn_shotnoise): one
+    particle per site of the neutrino lattice, at the site plus the Zel'dovich displacement,
+    with a thermal momentum of speed q = speed_quantile(u_0) and an isotropic direction
+    cos(theta) = 2 u_1 - 1, phi = 2 pi u_2 (uniforms (3, n_sites^3) in (0, 1), drawn
+    outside).  Returns (u, p) in site order."""
+    nc = noise.shape[0]
+    dc = box / nc
+    r, j0, sh = neutrino_site_offset(nc, n_sites)
+    s = displacement(delta_k(noise, box, pk), box, shift=sh * dc, k_fs=k_fs)
+    idx = (j0 + r * np.arange(n_sites)) % nc
+    s_site = s[:, idx][:, :, idx][:, :, :, idx].reshape(3, -1)
+    site = neutrinos.site_positions(n_sites, nc, box).T
+    uq, umu, uphi = (np.asarray(x, dtype=np.float64) for x in uniforms)
+    q = np.array([neutrinos.speed_quantile(v, masses_ev) for v in uq])
+    mu = 2.0 * umu - 1.0
+    phi = 2.0 * np.pi * uphi
+    sin_t = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    dirs = np.stack([sin_t * np.cos(phi), sin_t * np.sin(phi), mu])
+    x = site + D0 * s_site
+    p = gp0 * s_site + p_scale * q[None, :] * dirs
+    return pm.quantise(x, box), p

@@ -143,3 +143,25 @@ def particle_masses(n_cdm, n_nu, n_shell, n_fib, m_cdm, m_nu):
         shell = (np.arange(n_nu) // ndir) % n_shell
         out[n_cdm:] = np.asarray(m_nu)[shell]
     return out
+
+
+# ------------------------------------------------------------ pseudo-random sampling
+def speed_cdf(q, masses_ev, q_max=Q_MAX):
+    """Fraction of neutrinos with speed below q under the speed density q^2 f~(q) on
+    [0, q_max] (the phase-space measure of the distribution of Eq. FD_deg)."""
+    alphas = mass_ratios(masses_ev)
+    dens = lambda x: x * x * effective_fd(x, alphas)  # noqa: E731
+    total = _quad(dens, 0.0, q_max)
+    return _quad(dens, 0.0, min(float(q), q_max)) / total
+
+
+def speed_quantile(u, masses_ev, q_max=Q_MAX):
+    """Inverse of :func:`speed_cdf`: the speed below which a fraction u of neutrinos lies
+    (root of speed_cdf(q) = u by bisection-secant, to 1e-13)."""
+    from scipy.optimize import brentq
+    u = float(u)
+    if u <= 0.0:
+        return 0.0
+    if u >= 1.0:
+        return float(q_max)
+    return brentq(lambda q: speed_cdf(q, masses_ev, q_max) - u, 0.0, q_max, xtol=1e-13, rtol=1e-13)

@@ -142,3 +142,43 @@ def test_sites_are_staggered_from_cdm_lattice():
     dc = box / nc
     frac = (s / dc) % 1.0
     assert np.all(np.abs(frac - 0.5) < 1e-12)        # half a CDM spacing off every lattice plane
+
+
+def _fd2_integral(q):
+    """int_0^q x^2 / (e^x + 1) dx in closed form: -q^2 ln(1 + e^-q) + 2 q Li2(-e^-q)
+    + 2 Li3(-e^-q) + 3 zeta(3) / 2 (differentiate to check; zero at q = 0)."""
+    mpmath = pytest.importorskip("mpmath")
+    z = -mpmath.e ** (-q)
+    return float(-q * q * mpmath.log(1 + mpmath.e ** (-q)) + 2 * q * mpmath.polylog(2, z)
+                 + 2 * mpmath.polylog(3, z) + 1.5 * mpmath.zeta(3))
+
+
+@pytest.mark.parametrize("masses", [(0.1, 0.1, 0.1), (0.12, 0.06, 0.02)])
+def test_speed_cdf_matches_polylog_closed_form(masses):
+    """F(q) = sum_j alpha_j^4 int_0^q x^2 f(alpha_j x) dx / total; each term is
+    alpha_j^-3 times the closed form at alpha_j q."""
+    al = nu.mass_ratios(list(masses))
+    tot = sum(a ** 4 / a ** 3 * _fd2_integral(a * nu.Q_MAX) for a in al)
+    for q in (0.3, 1.0, 3.15, 7.0, 15.0):
+        ref = sum(a * _fd2_integral(a * q) for a in al) / tot
+        assert nu.speed_cdf(q, list(masses)) == pytest.approx(ref, rel=1e-10)
+
+
+def test_speed_quantile_inverts_cdf_and_reproduces_moments():
+    """q(F(q)) = q; the mean and mean square of q(u) over u in (0, 1) are the first two
+    moments of the speed density q^2 f(q): 7 pi^4 / (180 zeta(3)) and 15 zeta(5) / zeta(3)."""
+    import math
+    from scipy.special import zeta
+    m = [0.1, 0.1, 0.1]
+    for q in (0.5, 2.0, 6.0, 12.0):
+        assert nu.speed_quantile(nu.speed_cdf(q, m), m) == pytest.approx(q, rel=1e-10)
+    # Gauss-Legendre in t with u = 1 - (1 - t^3)^4: q ~ u^(1/3) ~ t near t = 0 and the
+    # q ~ -ln(1 - u) tail damped by (1 - t^3)^3 near t = 1
+    t, w = np.polynomial.legendre.leggauss(80)
+    t = 0.5 * (t + 1.0)
+    w = 0.5 * w
+    u = 1.0 - (1.0 - t ** 3) ** 4
+    du = 12.0 * t ** 2 * (1.0 - t ** 3) ** 3
+    q = np.array([nu.speed_quantile(v, m) for v in u])
+    assert float((w * du * q).sum()) == pytest.approx(7 * math.pi ** 4 / (180 * zeta(3)), rel=1e-6)
+    assert float((w * du * q * q).sum()) == pytest.approx(15 * zeta(5) / zeta(3), rel=1e-5)
