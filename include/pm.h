@@ -210,6 +210,17 @@ int pm_power(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int3
  * Writes st->u, st->p, st->id (canonical order), st->n, st->a = a0, st->f_valid = 0. */
 int pm_ic(pm_ctx* ctx, const float* noise, double a0, double k_fs, pm_state* st, void* stream);
 
+/* pm_ic with pseudo-random neutrinos (the comparison scheme of §3 Fig. Pn_shotnoise):
+ * requires nshell = 1 and nfib = 0, so one particle per site, placed at the site plus the
+ * Zel'dovich displacement (no shell offset), with a thermal momentum of speed
+ * q = F^-1(u_0) (F: CDF of the speed density q^2 f~(q) of Eq. FD_deg, tabulated in FP64
+ * at 8193 speeds in [0, 40] and inverted by linear interpolation) along the direction
+ * cos(theta) = 2 u_1 - 1, phi = 2 pi u_2.  uniforms: device, 3 x nsites^3 floats in
+ * [0, 1) (u_0 of every site, then u_1, then u_2), drawn by the caller.  PM_EINVAL if the
+ * configuration is not one particle per site. */
+int pm_ic_pseudo(pm_ctx* ctx, const float* noise, const float* uniforms, double a0, double k_fs,
+                 pm_state* st, void* stream);
+
 /* Checkpoint of a particle state (per-step checkpoints for resuming and for the
  * adjoint).  File: a 512-byte ASCII JSON header padded with spaces ({"format":
  * "pmnu-state-1", "n", "a", "f_valid", "nmesh", "box", "config_hash"}), then u[3n]

@@ -553,6 +553,13 @@ int pm_ic(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, v
   return ic_build(c, noise, a0, k_fs, st, S(stream));
 }
 
+int pm_ic_pseudo(pm_ctx* c, const float* noise, const float* uniforms, double a0, double k_fs,
+                 pm_state* st, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!noise || !uniforms || !st || !st->u || !st->p || !st->id) return PM_EINVAL;
+  return ic_build(c, noise, a0, k_fs, st, S(stream), uniforms);
+}
+
 namespace {
 // FNV-1a over the fields that define the physics and the mesh
 uint64_t config_hash(const pm_config& f) {

@@ -282,6 +282,36 @@ void Cosmo::coeffs(double a0, double ah, double a1, double out[3]) const {
   out[2] = (gp(a1) - gp(ah)) / gf(a1);
 }
 
+// ---------------------------------------------------------------- neutrino speeds
+int nu_speed_cdf_table(const double* masses, int nmass, double q_max, int nnodes, double* F) {
+  if (nmass < 1 || nnodes < 2 || !(q_max > 0.0)) return PM_EINVAL;
+  double mmax = 0.0;
+  for (int i = 0; i < nmass; ++i) mmax = std::max(mmax, masses[i]);
+  if (!(mmax > 0.0)) return PM_EINVAL;
+  auto dens = [&](double q) {
+    double s = 0.0;
+    for (int i = 0; i < nmass; ++i) {
+      const double al = masses[i] / mmax;
+      s += al * al * al * al / (std::exp(al * q) + 1.0);
+    }
+    return q * q * s;
+  };
+  // composite Simpson with 16 panels per table interval (the density is smooth)
+  const double h = q_max / (nnodes - 1);
+  F[0] = 0.0;
+  for (int i = 1; i < nnodes; ++i) {
+    const double a = (i - 1) * h, b = i * h;
+    const int m = 16;
+    const double dh = (b - a) / m;
+    double acc = dens(a) + dens(b);
+    for (int j = 1; j < m; ++j) acc += (j % 2 ? 4.0 : 2.0) * dens(a + j * dh);
+    F[i] = F[i - 1] + acc * dh / 3.0;
+  }
+  const double tot = F[nnodes - 1];
+  for (int i = 0; i < nnodes; ++i) F[i] /= tot;
+  return PM_OK;
+}
+
 // ---------------------------------------------------------------- neutrino shells
 int nu_shell_table(int n_shell, const double* masses, int nmass, double q_max, double* edges,
                    double* q_shell, double* m_shell) {

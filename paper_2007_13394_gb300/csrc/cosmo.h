@@ -46,6 +46,10 @@ double fd_integral_dy(double y);
 int nu_shell_table(int n_shell, const double* masses, int nmass, double q_max, double* edges,
                    double* q_shell, double* m_shell);
 
+// CDF of the neutrino speed density q^2 f~(q) (Eq. FD_deg over the given masses, relative
+// to the heaviest) on [0, q_max] at nnodes equally spaced q, normalised to F(q_max) = 1.
+int nu_speed_cdf_table(const double* masses, int nmass, double q_max, int nnodes, double* F);
+
 // BBKS transfer function T(k), k in h/Mpc
 double bbks(double k, double omega_m, double h);
 // amplitude A of P(k) = A k^ns T(k)^2 giving sigma_8 at z = 0

@@ -83,6 +83,39 @@ __global__ void k_ic_nu(const float* __restrict__ s, int nc, int rp, int comp, i
   p[comp * n_total + n_offset + k] = (float)(gp0 * (double)sv + pth * dcomp);
 }
 
+// Pseudo-random sampling: one particle per site, no shell offset, thermal momentum of
+// speed q = F^-1(u_0) (F tabulated at nF equally spaced q; bisection, then linear
+// interpolation inside the bracket) along cos(theta) = 2 u_1 - 1, phi = 2 pi u_2.
+__global__ void k_ic_nu_pseudo(const float* __restrict__ s, int nc, int rp, int comp, int nsites,
+                               int stride, int j0, double site_dx, double site_off, double D0,
+                               double gp0, double to_fix, double pscale, const double* __restrict__ F,
+                               int nF, double dq, const float* __restrict__ uni, int64_t n_offset,
+                               int64_t n_nu, uint32_t* __restrict__ u, float* __restrict__ p,
+                               int64_t n_total) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_nu) return;
+  const int sx = (int)(k / ((int64_t)nsites * nsites)), sy = (int)((k / nsites) % nsites),
+            sz = (int)(k % nsites);
+  const int ix = (j0 + stride * sx) % nc, iy = (j0 + stride * sy) % nc, iz = (j0 + stride * sz) % nc;
+  const float sv = s[((size_t)ix * nc + iy) * rp + iz];
+  const int sd = comp == 0 ? sx : (comp == 1 ? sy : sz);
+  const double uq = (double)uni[k], umu = (double)uni[n_nu + k], uphi = (double)uni[2 * n_nu + k];
+  int lo = 0, hi = nF - 1;  // F[lo] <= uq <= F[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (F[mid] <= uq) lo = mid; else hi = mid;
+  }
+  const double span = F[hi] - F[lo];
+  const double q = dq * (lo + (span > 0.0 ? (uq - F[lo]) / span : 0.0));
+  const double mu = 2.0 * umu - 1.0, phi = 6.283185307179586 * uphi;
+  const double st = sqrt(fmax(0.0, 1.0 - mu * mu));
+  const double dcomp = comp == 0 ? st * cos(phi) : (comp == 1 ? st * sin(phi) : mu);
+  const double x = (sd + 0.5) * site_dx + site_off + D0 * (double)sv;
+  const long long v = __double2ll_rn(x * to_fix);
+  u[comp * n_total + n_offset + k] = (uint32_t)(unsigned long long)v;
+  p[comp * n_total + n_offset + k] = (float)(gp0 * (double)sv + pscale * q * dcomp);
+}
+
 __global__ void k_iota(uint32_t* __restrict__ id, int64_t n) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) id[i] = (uint32_t)i;
@@ -90,8 +123,10 @@ __global__ void k_iota(uint32_t* __restrict__ id, int64_t n) {
 
 }  // namespace
 
-int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s) {
+int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s,
+             const float* uniforms) {
   const pm_config& cf = c->cfg;
+  if (uniforms && (cf.nsites <= 0 || cf.nshell != 1 || cf.nfib != 0)) return PM_EINVAL;
   const int nc = cf.nc;
   if (nc < 32 || (nc & (nc - 1)) || nc > c->g.n) return PM_EINVAL;
   if (cf.nsites > 0 && (nc % cf.nsites != 0)) return PM_EINVAL;
@@ -134,10 +169,22 @@ int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st
     PM_CUDA_TRY(cudaMemcpy(c->ic_amp, hc.data(), sizeof(float) * len, cudaMemcpyHostToDevice));
     PM_CUDA_TRY(cudaMemcpy(c->ic_amp_nu, hn.data(), sizeof(float) * len, cudaMemcpyHostToDevice));
   }
-  // neutrino table: radius[shell], p_th[shell], directions[ndir][3]
+  // neutrino table: radius[shell], p_th[shell], directions[ndir][3] (quasi-random), or the
+  // speed CDF at kNF equally spaced q in [0, 40] (pseudo-random)
+  constexpr int kNF = 8193;
+  constexpr double kQmax = 40.0;
   double* tab = nullptr;
   std::vector<double> htab;
-  if (n_nu > 0) {
+  double pscale_ps = 0.0;
+  if (n_nu > 0 && uniforms) {
+    double mmax = 0.0;
+    for (int i = 0; i < cf.n_nu; ++i) mmax = std::max(mmax, cf.m_nu[i]);
+    pscale_ps = c->cosmo.kT_nu0 / mmax * 2997.92458;
+    htab.resize(kNF);
+    if (nu_speed_cdf_table(cf.m_nu, cf.n_nu, kQmax, kNF, htab.data()) != PM_OK) return PM_EINVAL;
+    PM_CUDA_TRY(cudaMallocAsync(&tab, sizeof(double) * htab.size(), s));
+    PM_CUDA_TRY(cudaMemcpyAsync(tab, htab.data(), sizeof(double) * htab.size(), cudaMemcpyHostToDevice, s));
+  } else if (n_nu > 0) {
     const double qmax = *std::max_element(c->q_shell.begin(), c->q_shell.end());
     double mmax = 0.0;
     for (int i = 0; i < cf.n_nu; ++i) mmax = std::max(mmax, cf.m_nu[i]);
@@ -183,6 +230,10 @@ int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st
       if (species == 0) {
         k_ic_cdm<<<(unsigned)((n_cdm + 255) / 256), 256, 0, s>>>(
             sr, nc, 2 * gi.pc, comp, L / nc, D0, gp0, to_fix, 0, st->u, st->p, st->n);
+      } else if (uniforms) {
+        k_ic_nu_pseudo<<<(unsigned)((n_nu + 255) / 256), 256, 0, s>>>(
+            sr, nc, 2 * gi.pc, comp, cf.nsites, stride, j0, L / cf.nsites, 0.5 * L / nc, D0, gp0,
+            to_fix, pscale_ps, tab, kNF, kQmax / (kNF - 1), uniforms, n_cdm, n_nu, st->u, st->p, st->n);
       } else {
         k_ic_nu<<<(unsigned)((n_nu + 255) / 256), 256, 0, s>>>(
             sr, nc, 2 * gi.pc, comp, cf.nsites, stride, j0, L / cf.nsites, 0.5 * L / nc, D0, gp0,

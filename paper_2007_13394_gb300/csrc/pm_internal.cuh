@@ -202,7 +202,8 @@ void repack_complex(pm_ctx* c, const Geom& g, const float2* src, int src_pitch, 
 int power_bin(pm_ctx* c, const float2* da, const float2* db, int nbins, double* k_out,
               double* P_out, int64_t* nmodes_out, cudaStream_t s);
 int power_weight(pm_ctx* c, int nbins, const double* dL_dP, cudaStream_t s);
-int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s);
+int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st, cudaStream_t s,
+             const float* uniforms = nullptr);
 float2* twiddles(pm_ctx* c, int n);
 // adjoint (k_adjoint.cu)
 void readout_grad(pm_ctx* c, int64_t n, const float* const* meshes, int nmeshes, int row_pitch,

@@ -54,3 +54,9 @@ def mlp_parameters(seed: int, hidden: int = 64, last_scale: float = 0.0) -> np.n
              u(hidden * hidden, 1 / np.sqrt(hidden)), u(hidden, 1 / np.sqrt(hidden)),
              u(hidden, last_scale / np.sqrt(hidden)), u(1, last_scale / np.sqrt(hidden))]
     return np.concatenate(parts).astype(np.float32)
+
+
+def uniform_values(shape, seed: int) -> np.ndarray:
+    """Uniform random float32 values in [0, 1) (the draws of pseudo-random sampling)."""
+    rng = np.random.default_rng(seed)
+    return rng.random(shape, dtype=np.float32)

@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_step_host": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, ctypes.POINTER(i32), d, d, d, vp]),
         "pm_power": (ctypes.c_int, [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
         "pm_ic": (ctypes.c_int, [vp, vp, d, d, ctypes.POINTER(State), vp]),
+        "pm_ic_pseudo": (ctypes.c_int, [vp, vp, vp, d, d, ctypes.POINTER(State), vp]),
         "pm_state_save": (ctypes.c_int, [vp, ctypes.POINTER(State), ctypes.c_char_p]),
         "pm_state_load": (ctypes.c_int, [vp, ctypes.POINTER(State), ctypes.c_char_p]),
         "pm_fft_r2c": (ctypes.c_int, [vp, vp, vp, vp]),
@@ -337,6 +338,18 @@ class ParticleMesh:
         s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
                   st["u"].shape[1], a0, 0, 0)
         _check(self.lib.pm_ic(self.h, _ptr(noise), a0, k_fs, ctypes.byref(s), _stream()), "pm_ic")
+        st["a"], st["f_valid"] = s.a, s.f_valid
+        return st
+
+    def ic_pseudo(self, noise, uniforms, a0, k_fs=0.0):
+        """Zel'dovich ICs with pseudo-random neutrino speeds and directions (one particle per
+        site; the configuration must have nshell = 1, nfib = 0).  uniforms: device float32
+        (3, nsites^3) in [0, 1)."""
+        st = self.new_state(self.cfg.n_particles())
+        s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
+                  st["u"].shape[1], a0, 0, 0)
+        _check(self.lib.pm_ic_pseudo(self.h, _ptr(noise), _ptr(uniforms), a0, k_fs, ctypes.byref(s), _stream()),
+               "pm_ic_pseudo")
         st["a"], st["f_valid"] = s.a, s.f_valid
         return st
 
