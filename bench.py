@@ -13,6 +13,7 @@ on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -241,6 +242,8 @@ def run_ours(args):
     cfg = workloads.PRESETS[args.config]()
     if args.two_mesh:
         cfg.flags |= 1
+    if args.no_nu:  # the same run without neutrino particles (massless neutrinos)
+        cfg = dataclasses.replace(cfg, nsites=0, m_nu=(0.0, 0.0, 0.0))
     ctx = pm.ParticleMesh(cfg)
     n = cfg.n_particles()
     # initial conditions on the GPU from seeded white noise (one independent replica per rank)
@@ -372,6 +375,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg_mid", "cfg3"], default="cfg2")
     ap.add_argument("--two-mesh", action="store_true", help="per-component force path (flags bit 0)")
+    ap.add_argument("--no-nu", action="store_true",
+                    help="the same workload without neutrino particles (massless neutrinos)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

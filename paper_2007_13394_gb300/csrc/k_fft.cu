@@ -228,7 +228,7 @@ void launch_x_fused(float2* a, float2* b, float2* cz, int pc, const float2* tw, 
 
 template <int LOGM>
 constexpr int tk_for() {
-  return LOGM >= 11 ? 4 : (LOGM == 10 ? 8 : 16);
+  return LOGM >= 10 ? 8 : 16;
 }
 
 template <int LOGM, bool INV, int EPI, int PRO>
