@@ -125,17 +125,21 @@ def algorithmic_bytes(kind, n_mesh, n_particles):
     return table.get(kind)
 
 
-def source_digest():
+def source_digest(files=None):
+    """sha256 prefix of the given CUDA source files (default: all of them)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2007_13394_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files or os.listdir(d)):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture,
-# keyed by (kernel kind, workload); valid only while the CUDA sources hash to the stated digest.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# (profiles/ncu_fft_y_cfg2.md), keyed by (kernel kind, workload): (bytes, digest, the source
+# files that define the kernel).  Reported only while those files hash to the digest.
+NCU_TRAFFIC = {
+    ("fft_y", "cfg2"): (1.0331e9, "9b1979108d3d", ("fft_engine.cuh", "k_fft_tma.cu")),
+}
 
 
 def dist_setup(args):
@@ -313,7 +317,7 @@ def run_ours(args):
         achieved = alg / (dom_ms / 1e3) / 1e9 if alg and dom_ms > 0 else None
         key = (dominant, args.config)
         traffic = None
-        if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_digest():
+        if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_digest(NCU_TRAFFIC[key][2]):
             traffic = NCU_TRAFFIC[key][0]
         roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
