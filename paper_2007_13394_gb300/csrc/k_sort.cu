@@ -7,8 +7,9 @@
 // digits (two 9-bit passes cover the 18-bit keys of meshes up to 512^3):
 // per pass, an upsweep histogram per 4096-key block, a scan of the
 // digit-major histogram, and a downsweep that ranks each key stably inside
-// its block (warp match + per-warp prefix, rounds in index order) and writes
-// it through shared memory so that global writes stay coalesced.
+// its block (warp match inside a round, warp-private digit counters across the
+// warp's contiguous 512 keys, one block scan over (digit, warp)) and writes it
+// through shared memory so that global writes stay coalesced.
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"
@@ -134,6 +135,11 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __
   }
 }
 
+// Stable scatter of one 4096-key block: warp w ranks the contiguous keys [512 w, 512 w + 512)
+// of the block in 16 rounds of 32 (warp match for the rank inside a round, a warp-private
+// per-digit counter across rounds), so the order inside each digit is the index order;
+// one block-wide scan over (digit, warp) turns the counters into staging offsets; the
+// keys are staged in digit order in shared memory and written out in coalesced runs.
 template <int BITS>
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift,
@@ -141,75 +147,90 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
   constexpr int DIG = 1 << BITS, PER = DIG / kRadixThreads;
   constexpr uint32_t MASK = DIG - 1;
+  constexpr int KPW = kRadixTile / kRadixWarps;  // keys per warp
+  constexpr int RPW = KPW / 32;                  // rounds per warp
   extern __shared__ uint32_t stage_kv[];  // keys then values of the block, in digit order
   uint32_t* sk = stage_kv;
   uint32_t* sv = stage_kv + kRadixTile;
-  __shared__ uint32_t wcnt[kRadixWarps][DIG];
-  __shared__ uint32_t running[DIG];
-  __shared__ uint32_t dstart[DIG];  // block-local start of each digit
-  __shared__ uint32_t gbase[DIG];   // global start of this block's run of each digit
+  __shared__ uint32_t wcnt[kRadixWarps][DIG];  // per-warp digit counts, then staging offsets
+  __shared__ uint32_t dstart[DIG];             // block-local start of each digit
+  __shared__ uint32_t gbase[DIG];              // global start of this block's run of each digit
   __shared__ uint32_t ws[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-  {  // thread t owns digits t * PER .. t * PER + PER - 1 for the block-local scan
+  for (int i = t; i < kRadixWarps * DIG; i += kRadixThreads) (&wcnt[0][0])[i] = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int d = t + q * kRadixThreads;
+    gbase[d] = hist_scan[(long long)d * nblk + blockIdx.x];
+  }
+  __syncthreads();
+  // 1. ranks inside the warp's digit runs
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t key[RPW], val[RPW], rk[RPW];
+#pragma unroll
+  for (int r = 0; r < RPW; ++r) {
+    const int64_t i = base + w * KPW + r * 32 + lane;
+    const bool ok = i < n;
+    key[r] = ok ? kin[i] : 0u;
+    val[r] = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
+    const uint32_t d = ok ? ((key[r] >> shift) & MASK) : (uint32_t)(DIG + lane);
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t below = (uint32_t)__popc(peers & lt);
+    const uint32_t c0 = ok ? wcnt[w][d] : 0u;  // every peer reads the count before this round
+    rk[r] = c0 + below;
+    __syncwarp();
+    if (ok && below == 0) wcnt[w][d] = c0 + (uint32_t)__popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // 2. digit totals -> block-exclusive digit starts -> per-warp staging offsets
+  {
     uint32_t c[PER], sum = 0;
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int d = t * PER + q;
-      c[q] = hist[(long long)d * nblk + blockIdx.x];
-      gbase[d] = hist_scan[(long long)d * nblk + blockIdx.x];
-      running[d] = 0;
-      sum += c[q];
+      uint32_t tot = 0;
+#pragma unroll
+      for (int ww = 0; ww < kRadixWarps; ++ww) tot += wcnt[ww][d];
+      c[q] = tot;
+      sum += tot;
     }
     uint32_t ex = block_exclusive_scan(sum, ws, nullptr);
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
-      dstart[t * PER + q] = ex;
+      const int d = t * PER + q;
+      dstart[d] = ex;
+      uint32_t run = ex;
+#pragma unroll
+      for (int ww = 0; ww < kRadixWarps; ++ww) {
+        const uint32_t cw = wcnt[ww][d];
+        wcnt[ww][d] = run;
+        run += cw;
+      }
       ex += c[q];
     }
   }
   __syncthreads();
-  for (int r = 0; r < kRadixRounds; ++r) {
+  // 3. stage in digit order
 #pragma unroll
-    for (int q = 0; q < kRadixWarps; ++q)
-#pragma unroll
-      for (int p = 0; p < PER; ++p) wcnt[q][t + p * kRadixThreads] = 0;
-    __syncthreads();
-    int64_t i = base + r * kRadixThreads + t;
-    bool ok = i < n;
-    uint32_t key = ok ? kin[i] : 0u;
-    uint32_t val = ok ? (vin ? vin[i] : (uint32_t)i) : 0u;
-    uint32_t d = ok ? ((key >> shift) & MASK) : (uint32_t)(DIG + lane);
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    int rank_w = __popc(peers & ((1u << lane) - 1u));
-    if (ok && rank_w == 0) wcnt[w][d] = __popc(peers);
-    __syncthreads();
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {  // prefix over warps for each owned digit
-      const int dd = t + p * kRadixThreads;
-      uint32_t acc = running[dd];
-#pragma unroll
-      for (int q = 0; q < kRadixWarps; ++q) {
-        uint32_t c = wcnt[q][dd];
-        wcnt[q][dd] = acc;
-        acc += c;
-      }
-      running[dd] = acc;
+  for (int r = 0; r < RPW; ++r) {
+    const int64_t i = base + w * KPW + r * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (key[r] >> shift) & MASK;
+      const uint32_t pos = wcnt[w][d] + rk[r];
+      sk[pos] = key[r];
+      sv[pos] = val[r];
     }
-    __syncthreads();
-    if (ok) {
-      uint32_t pos = dstart[d] + wcnt[w][d] + rank_w;
-      sk[pos] = key;
-      sv[pos] = val;
-    }
-    __syncthreads();
   }
+  __syncthreads();
+  // 4. coalesced runs to the digit's global position
   const int64_t cnt = (n - base) < kRadixTile ? (n - base) : kRadixTile;
   for (int j = t; j < cnt; j += kRadixThreads) {
-    uint32_t key = sk[j];
-    uint32_t d = (key >> shift) & MASK;
+    uint32_t k = sk[j];
+    uint32_t d = (k >> shift) & MASK;
     uint32_t dst = gbase[d] + (j - dstart[d]);
-    kout[dst] = key;
+    kout[dst] = k;
     vout[dst] = sv[j];
   }
 }
