@@ -327,10 +327,11 @@ def run_ours(args):
         # end to end through the C-ABI with host buffers: copies in, step, copies out, every step
         e2e = None
         if not args.no_e2e and args.config not in ("cfg3", "cfg_mid"):
-            hu = pm.to_u32(st["u"]).copy()
-            hp = st["p"].cpu().numpy().copy()
-            hid = pm.to_u32(st["id"]).copy()
-            hf = st["f"].cpu().numpy().copy()
+            # pinned (page-locked) host buffers, viewed as numpy arrays for the C-ABI call
+            pinned = {k: torch.empty(st[k].shape, dtype=st[k].dtype, pin_memory=True) for k in ("u", "p", "id", "f")}
+            for k, v in pinned.items():
+                v.copy_(st[k])
+            hu, hp, hid, hf = (pinned[k].numpy() for k in ("u", "p", "id", "f"))
             fv = st["f_valid"]
             k_e2e = max(3, min(args.steps, 10))
             base = args.warmup + args.steps
@@ -342,7 +343,8 @@ def run_ours(args):
             t_e2e = (time.perf_counter() - t0) / k_e2e
             e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 40 * n,
                    "d2h_bytes_per_step": 40 * n, "steps": k_e2e,
-                   "note": "pm_step_host: u, p, id, f copied host->device, one KDK step, copied back"}
+                   "note": "pm_step_host: u, p, id, f copied from pinned host memory to the device, "
+                           "one KDK step, copied back"}
         cpu = None
         if not args.no_cpu_baseline and world == 1 and args.config not in ("cfg3", "cfg_mid"):
             ocfg, desc = oracle_sample_cfg(1)
