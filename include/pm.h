@@ -81,7 +81,7 @@ enum {
 enum { PM_SPECIES_CDM = 1, PM_SPECIES_NU = 2, PM_SPECIES_ALL = 3 };
 
 /* pm_config.flags bits. */
-enum { PM_FLAG_TWO_MESH = 1, PM_FLAG_SPECTRAL_KERNEL = 2 };
+enum { PM_FLAG_TWO_MESH = 1, PM_FLAG_SPECTRAL_KERNEL = 2, PM_FLAG_MLP_TENSOR = 4 };
 
 /* Run configuration.  Zero-initialise, then set the fields. */
 typedef struct pm_config {
@@ -104,7 +104,9 @@ typedef struct pm_config {
   double sigma8;       /* normalisation of the synthetic initial spectrum (pm_ic) */
   uint32_t flags;      /* bit 0 (PM_FLAG_TWO_MESH): two-mesh per-component force path (less
                           memory; always used for nmesh = 2048); bit 1 (PM_FLAG_SPECTRAL_KERNEL):
-                          deconvolved spectral force kernel; other bits 0 */
+                          deconvolved spectral force kernel; bit 2 (PM_FLAG_MLP_TENSOR): the
+                          learned factor's table on the tensor cores (BF16 operands, FP32
+                          accumulation) instead of FP32; other bits 0 */
   int32_t pad1;
 } pm_config;
 
@@ -290,6 +292,10 @@ int pm_get_mlp(pm_ctx* ctx, float* theta, int64_t nparam);
 /* Scale factor at which pm_force, pm_potential and pm_force_vjp evaluate the factor
  * (default 1); pm_step and pm_step_vjp use their own a0 and a1. */
 int pm_set_force_time(pm_ctx* ctx, double a);
+/* The table the Green's-function passes read at scale factor a: out[s] = m(sqrt(s) /
+ * (N/2), a) for s = 0 .. 3 (N/2)^2 (device, 3 (N/2)^2 + 1 floats); computed the way the
+ * context computes it (FP32, or tensor cores with PM_FLAG_MLP_TENSOR). */
+int pm_mlp_table(pm_ctx* ctx, double a, float* out, void* stream);
 /* m at n points (device arrays kappa[n], a[n] -> m_out[n]). */
 int pm_mlp_eval(pm_ctx* ctx, const float* kappa, const float* a, int64_t n, float* m_out, void* stream);
 /* With the factor on, pm_force_vjp and pm_step_vjp also accumulate d L / d theta of

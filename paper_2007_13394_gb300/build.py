@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O3"]
 SOURCES = ["cosmo.cpp", "capi.cu", "k_sort.cu", "k_particles.cu", "k_fft.cu", "k_power.cu",
-           "k_ic.cu", "k_power_noalloc.cu", "k_fft_tma.cu", "k_adjoint.cu", "k_mlp.cu"]
+           "k_ic.cu", "k_power_noalloc.cu", "k_fft_tma.cu", "k_adjoint.cu", "k_mlp.cu", "k_mlp_tc.cu"]
 
 
 def nvcc() -> str:

@@ -335,6 +335,10 @@ void mlp_free(pm_ctx* c) {
 
 void mlp_table(pm_ctx* c, double a, cudaStream_t s) {
   if (!c->mlp_on) return;
+  if (c->cfg.flags & PM_FLAG_MLP_TENSOR) {
+    mlp_table_tc(c, a, s);
+    return;
+  }
   LaunchScope L(c, s, K_MLP_TABLE);
   const unsigned grid = (unsigned)std::min<int64_t>(nblocks(c->mlp_ntab), 4 * 152);
   k_mlp_table<<<grid, 256, 0, s>>>(c->mlp_theta, (float)a, 2.0f / (float)c->g.n, c->mlp_ntab, c->mlp_tab);
@@ -395,6 +399,18 @@ int pm_mlp_eval(pm_ctx* c, const float* kappa, const float* a, int64_t n, float*
   LaunchScope L(c, s, K_MLP_MISC);
   const unsigned grid = (unsigned)std::min<int64_t>(nblocks(n), 4 * 152);
   k_mlp_eval<<<grid, 256, 0, s>>>(c->mlp_theta, kappa, a, n, m_out);
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+int pm_mlp_table(pm_ctx* c, double a, float* out, void* stream) {
+  if (!c || c->magic != kMagic) return PM_ENOTINIT;
+  if (!c->mlp_theta || !out || !(a > 0.0) || a > 2.0) return PM_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool on = c->mlp_on;
+  c->mlp_on = true;  // evaluate even while the factor is switched off
+  mlp_table(c, a, s);
+  c->mlp_on = on;
+  PM_CUDA_TRY(cudaMemcpyAsync(out, c->mlp_tab, sizeof(float) * c->mlp_ntab, cudaMemcpyDeviceToDevice, s));
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
 

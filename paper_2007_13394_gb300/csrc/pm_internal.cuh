@@ -222,6 +222,7 @@ int mlp_set(pm_ctx* c, const float* theta_host, int64_t nparam);
 void mlp_free(pm_ctx* c);
 // refreshes the |n|^2 table for scale factor a when the learned factor is on
 void mlp_table(pm_ctx* c, double a, cudaStream_t s);
+void mlp_table_tc(pm_ctx* c, double a, cudaStream_t s);  // tensor-core form (k_mlp_tc.cu)
 // phi_k = c(k) m(k) rho_k on the force mesh's half spectrum (src and dst padded)
 void mlp_green_apply(pm_ctx* c, const float2* rho_k, float2* phi_k, cudaStream_t s);
 // d L / d theta += backward of the network over mlp_gbin at scale factor a; clears mlp_gbin

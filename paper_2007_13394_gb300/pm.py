@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpmnu.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
 SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
 MLP_HIDDEN, MLP_NPARAM = 64, 4417
+FLAG_TWO_MESH, FLAG_SPECTRAL_KERNEL, FLAG_MLP_TENSOR = 1, 2, 4
 
 
 class PMError(RuntimeError):
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_get_mlp": (ctypes.c_int, [vp, vp, i64]),
         "pm_set_force_time": (ctypes.c_int, [vp, d]),
         "pm_mlp_eval": (ctypes.c_int, [vp, vp, vp, i64, vp, vp]),
+        "pm_mlp_table": (ctypes.c_int, [vp, d, vp, vp]),
         "pm_mlp_grad": (ctypes.c_int, [vp, vp, i64, i32, vp]),
         "pm_mlp_adam": (ctypes.c_int, [vp, vp, i64, d, d, d, d, i64, vp]),
         "pm_displacement_loss": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i32, vp, dp, vp]),
@@ -468,6 +470,13 @@ class ParticleMesh:
         out = torch.empty_like(kappa)
         _check(self.lib.pm_mlp_eval(self.h, _ptr(kappa), _ptr(a), kappa.numel(), _ptr(out), _stream()),
                "pm_mlp_eval")
+        return out
+
+    def mlp_table(self, a):
+        """The factor's table m(sqrt(s) / (N/2), a), s = 0 .. 3 (N/2)^2, as the context computes it."""
+        torch = _torch()
+        out = torch.empty(3 * (self.n // 2) ** 2 + 1, dtype=torch.float32, device="cuda")
+        _check(self.lib.pm_mlp_table(self.h, a, _ptr(out), _stream()), "pm_mlp_table")
         return out
 
     def mlp_grad(self, reset=True):

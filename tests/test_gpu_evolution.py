@@ -100,6 +100,49 @@ def test_ten_step_run_power_spectra_match_oracle(pm):
     ctx.sync()
 
 
+def test_cfg2_physics_power_spectra_match_oracle_at_128(pm):
+    """The cfg2 physics checked against the oracle run at 128^3: 256 Mpc/h, 128^3 CDM + 16^3 x
+    70 neutrinos (M_nu = 0.1 eV, free-streaming-suppressed initial neutrino field), mesh 256^3,
+    the paper's 25-step schedule from z = 99 to 0, both runs from the oracle's ICs: P_cdm, P_m
+    and P_cdm,nu at z = 0 within 0.1 % for k < k_Ny / 2.  (Slow: the FP64 oracle takes
+    several minutes.)"""
+    from paper_2007_13394_gb300 import workloads
+    cfg = workloads.cfg2_parity()
+    sched = workloads.schedule_paper(25)
+    a0 = sched[0][0]
+    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, a0, 1, workloads.free_streaming_k(cfg, a0))
+    f = opm.force(u, mass, cfg.nmesh, cfg.box, bg.omega_m0)
+    uo, po = u.copy(), p.copy()
+    for (a, ah, b) in sched:
+        uo, po, f = opm.kdk_step(uo, po, f, obg.step_coefficients(bg, a, ah, b), mass, cfg.nmesh, cfg.box,
+                                 bg.omega_m0)
+    ctx = pm.ParticleMesh(cfg)
+    st = ctx.new_state(u.shape[1])
+    st["u"].copy_(pm.as_u32_tensor(u))
+    st["p"].copy_(torch.from_numpy(p.astype(np.float32)))
+    st["id"].copy_(torch.arange(u.shape[1], dtype=torch.int32))
+    for (a, ah, b) in sched:
+        ctx.step(st, a, ah, b)
+    ctx.sync()
+    nb = cfg.nmesh // 4
+    kny = np.pi * cfg.nmesh / cfg.box
+    sel_c = np.arange(u.shape[1]) < ncdm
+    meshes = {1: opm.paint(uo[:, sel_c], mass[sel_c], cfg.nmesh),
+              2: opm.paint(uo[:, ~sel_c], mass[~sel_c], cfg.nmesh),
+              3: opm.paint(uo, mass, cfg.nmesh)}
+    ref = {ab: opm.power_spectrum(meshes[ab[0]], meshes[ab[1]], cfg.box, nb) for ab in ((1, 1), (2, 2), (3, 3), (1, 2))}
+    for (sa, sb) in ((1, 1), (3, 3), (1, 2)):
+        k, P, nm = ctx.power(st["u"], st["id"], species_a=sa, species_b=sb, nbins=nb)
+        ko, Po, no = ref[(sa, sb)]
+        sel = (no > 0) & (ko < kny / 2)
+        # the cross-spectrum crosses zero: measure it against its Cauchy-Schwarz bound
+        scale = np.abs(Po) if sa == sb else np.sqrt(ref[(1, 1)][1] * ref[(2, 2)][1])
+        rel = np.abs(P[sel] - Po[sel]) / scale[sel]
+        print(f"\nP_{sa}{sb}: max |P - P_oracle| / scale for k < k_Ny/2 = {rel.max():.2e}")
+        assert rel.max() < 1e-3, f"P_{sa}{sb}"
+    ctx.sync()
+
+
 def test_step_host_equals_device_step(pm):
     from paper_2007_13394_gb300 import workloads
     cfg = workloads.cfg1()

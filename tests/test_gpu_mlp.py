@@ -182,3 +182,41 @@ def test_power_vjp_matches_oracle(pm):
     ctx.sync()
     ref = om.power_vjp(u, rec.mass, cfg.nmesh, cfg.box, nb, dL_dP)[:, order]
     assert _rel(g.double().cpu().numpy(), ref) < 1e-4
+
+
+@pytest.mark.parametrize("nmesh", [64, 256])
+def test_mlp_tables_fp32_and_tensor_core_match_oracle(pm, nmesh):
+    """The |n|^2 table of the factor: FP32 (default) within 2e-6 of the FP64 network, the
+    tensor-core form (tcgen05, BF16 operands, FP32 accumulation) within the BF16 bound,
+    max error < 1 % of max |m - 1|."""
+    th = _theta(21, last=1.0)
+    th64 = th.astype(np.float64)
+    ctx32 = pm.ParticleMesh(_cfg(pm, nmesh=nmesh))
+    ctxtc = pm.ParticleMesh(_cfg(pm, nmesh=nmesh, flags=pm.FLAG_MLP_TENSOR))
+    ctx32.set_mlp(th)
+    ctxtc.set_mlp(th)
+    for a in (0.05, 0.5, 1.0):
+        t32 = ctx32.mlp_table(a).double().cpu().numpy()
+        ttc = ctxtc.mlp_table(a).double().cpu().numpy()
+        ctxtc.sync()
+        s = np.arange(t32.size)
+        ref = om.forward(th64, np.sqrt(s) / (nmesh / 2), a)
+        scale = np.abs(ref - 1.0).max()
+        assert np.abs(t32 - ref).max() < 2e-6 * max(1.0, np.abs(ref).max())
+        err = np.abs(ttc - ref).max() / scale
+        print(f"\nnmesh {nmesh} a {a}: tensor-core table max error / max|m-1| = {err:.2e}")
+        assert err < 1e-2
+
+
+def test_learned_force_with_tensor_core_table(pm):
+    cfg = _cfg(pm, flags=pm.FLAG_MLP_TENSOR)
+    ctx = pm.ParticleMesh(cfg)
+    rec = oad.Reconstruction(cfg, [], 0.1)
+    u, _ = rec.ics(inputs.white_noise(cfg.nc, seed=3).astype(np.float64))
+    th = _theta(4)
+    ctx.set_mlp(th)
+    ctx.set_force_time(0.37)
+    F = ctx.force(pm.as_u32_tensor(u), None).double().cpu().numpy()
+    ctx.sync()
+    ref = om.force(u, rec.mass, cfg.nmesh, cfg.box, rec.bg.omega_m0, th.astype(np.float64), 0.37)
+    assert _rel(F, ref) < 3e-3
