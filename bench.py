@@ -231,6 +231,42 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def fft_reference(ctx, n, reps=10):
+    """Our 3D r2c / c2r (the z, y, x passes of pm_fft_r2c / pm_fft_c2r, timed per kernel
+    with CUDA events, without the stage calls' layout repacks) beside cuFFT (through
+    torch.fft.rfftn / irfftn, out of place) on the same N^3 mesh, ms per transform."""
+    import torch
+    mesh = torch.randn((n, n, n), dtype=torch.float32, device="cuda")
+    out = {"mesh": n}
+    c = ctx.fft_r2c(mesh)
+    ctx.fft_c2r(c)
+    ctx.profile(None)
+    for name, fn in (("ours_r2c_ms", lambda: ctx.fft_r2c(mesh)), ("ours_c2r_ms", lambda: ctx.fft_c2r(c))):
+        ctx.profile_read(reset=True)
+        for _ in range(reps):
+            fn()
+        prof = ctx.profile_read(reset=True)
+        out[name] = round(sum(ms for kind, (ms, _) in prof.items() if kind != "repack") / reps, 4)
+    ctx.profile([])
+    y = torch.fft.rfftn(mesh)
+    torch.fft.irfftn(y, s=mesh.shape)
+    for name, fn in (("cufft_r2c_ms", lambda: torch.fft.rfftn(mesh)),
+                     ("cufft_c2r_ms", lambda: torch.fft.irfftn(y, s=mesh.shape))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / reps, 4)
+    out["note"] = ("ours: z, y, x passes of pm_fft_r2c / pm_fft_c2r (CUDA events per kernel, repacks "
+                   "excluded); cuFFT: torch.fft.rfftn / irfftn out of place; reference point only")
+    del mesh, c, y
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -345,6 +381,9 @@ def run_ours(args):
                    "d2h_bytes_per_step": 40 * n, "steps": k_e2e,
                    "note": "pm_step_host: u, p, id, f copied from pinned host memory to the device, "
                            "one KDK step, copied back"}
+        fft_ref = None
+        if args.config not in ("cfg3", "cfg_mid"):  # the 2048^3 / 1024^3 meshes: skipped (memory, time)
+            fft_ref = fft_reference(ctx, cfg.nmesh)
         cpu = None
         if not args.no_cpu_baseline and world == 1 and args.config not in ("cfg3", "cfg_mid"):
             ocfg, desc = oracle_sample_cfg(1)
@@ -364,6 +403,7 @@ def run_ours(args):
                              f"{cfg.nmesh ** 2 * (cfg.nmesh // 2 + 2) * 8 / 1e6:.0f} MB, particles "
                              f"{40 * n / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "fft_reference": fft_ref,
             "clocks": clk.summary(), "kernels_steady_step": per_kind,
         }
         print(json.dumps(out))

@@ -29,13 +29,18 @@ namespace {
 
 using namespace fft;
 
-constexpr int kZThreads = 256;
+// z-pass CTA size: 128 threads (two rows) from 2048-point rows up, so that more CTAs in
+// different load / transform / store phases share an SM; 256 below
+template <int LOGN>
+constexpr int z_threads() {
+  return LOGN >= 11 ? 128 : 256;
+}
 
 // z pass, real -> complex, in place on rows of pitch P float2.
-template <int LOGN>
-__global__ void __launch_bounds__(kZThreads, 4) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
-                                                         int pc, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
+template <int LOGN, int NT = z_threads<LOGN>()>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
+                                                          int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
   constexpr int LS = M + M / 16 + 2;  // line stride in shared memory
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
@@ -63,10 +68,10 @@ __global__ void __launch_bounds__(kZThreads, 4) k_fft_z_r2c(float2* __restrict__
 }
 
 // z pass, complex -> real, in place.
-template <int LOGN>
-__global__ void __launch_bounds__(kZThreads, 4) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
-                                                         int pc, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
+template <int LOGN, int NT = z_threads<LOGN>()>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
+                                                          int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
   constexpr int LS = M + M / 16 + 2;
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
@@ -249,6 +254,7 @@ void launch_strided(const float2* src, float2* dst, int axis, int pc, const floa
 
 template <int LOGN>
 void launch_z(float2* data, long long nrows, int pc, const float2* tw, bool inverse, cudaStream_t s) {
+  constexpr int kZThreads = z_threads<LOGN>();
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
   constexpr int LS = M + M / 16 + 2;
   const size_t smem = sizeof(float2) * (size_t)LS * LPC;
