@@ -116,6 +116,9 @@ def algorithmic_bytes(kind, n_mesh, n_particles):
         # u, p, id read; p, f, u, id written (tile order); three meshes read once
         "readout3_kick": 68 * n_particles + 12 * cells,
         "fft_x_plain": 2 * half,
+        "fft_x_potential": 2 * half,                            # forward, Green's function, inverse
+        # u, p, id read; p, f, u, id written (tile order); the potential read once
+        "readout_fd4_kick": 68 * n_particles + 4 * cells,
         "kick_drift_keys": 64 * n_particles,
         "gather": 64 * n_particles,
         "radix_scatter": 16 * n_particles,
@@ -280,8 +283,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     _build.build()
     cfg = workloads.PRESETS[args.config]()
+    if args.kspace_gradient:
+        cfg.flags |= 8
     if args.two_mesh:
-        cfg.flags |= 1
+        cfg.flags |= 1 | 8
     if args.no_nu:  # the same run without neutrino particles (massless neutrinos)
         cfg = dataclasses.replace(cfg, nsites=0, m_nu=(0.0, 0.0, 0.0))
     ctx = pm.ParticleMesh(cfg)
@@ -399,7 +404,7 @@ def run_ours(args):
                                    f"{cfg.nshell * (2 * cfg.nfib + 1)} nu (M_nu = {sum(cfg.m_nu):g} eV), "
                                    f"mesh {cfg.nmesh}^3, one KDK PM step",
                        "n_particles": n, "nmesh": cfg.nmesh, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (two padded meshes of "
+                       "l2": "inputs larger than L2 (padded force mesh of "
                              f"{cfg.nmesh ** 2 * (cfg.nmesh // 2 + 2) * 8 / 1e6:.0f} MB, particles "
                              f"{40 * n / 1e6:.0f} MB)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -420,7 +425,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg_mid", "cfg3"], default="cfg2")
-    ap.add_argument("--two-mesh", action="store_true", help="per-component force path (flags bit 0)")
+    ap.add_argument("--kspace-gradient", action="store_true",
+                    help="gradient in k-space with three inverse transforms (flags bit 3)")
+    ap.add_argument("--two-mesh", action="store_true",
+                    help="k-space gradient one component at a time (flags bits 0 and 3)")
     ap.add_argument("--no-nu", action="store_true",
                     help="the same workload without neutrino particles (massless neutrinos)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -81,7 +81,7 @@ enum {
 enum { PM_SPECIES_CDM = 1, PM_SPECIES_NU = 2, PM_SPECIES_ALL = 3 };
 
 /* pm_config.flags bits. */
-enum { PM_FLAG_TWO_MESH = 1, PM_FLAG_SPECTRAL_KERNEL = 2, PM_FLAG_MLP_TENSOR = 4 };
+enum { PM_FLAG_TWO_MESH = 1, PM_FLAG_SPECTRAL_KERNEL = 2, PM_FLAG_MLP_TENSOR = 4, PM_FLAG_KSPACE_GRADIENT = 8 };
 
 /* Run configuration.  Zero-initialise, then set the fields. */
 typedef struct pm_config {
@@ -102,11 +102,17 @@ typedef struct pm_config {
   int64_t n_max;       /* capacity of the sort scratch (>= every n passed later) */
   double ns;           /* spectral index of the synthetic initial spectrum (pm_ic) */
   double sigma8;       /* normalisation of the synthetic initial spectrum (pm_ic) */
-  uint32_t flags;      /* bit 0 (PM_FLAG_TWO_MESH): two-mesh per-component force path (less
-                          memory; always used for nmesh = 2048); bit 1 (PM_FLAG_SPECTRAL_KERNEL):
-                          deconvolved spectral force kernel; bit 2 (PM_FLAG_MLP_TENSOR): the
-                          learned factor's table on the tensor cores (BF16 operands, FP32
-                          accumulation) instead of FP32; other bits 0 */
+  uint32_t flags;      /* Default force path: one potential mesh phi (forward FFT, Green's
+                          function, inverse FFT, all in place) and the 4-point gradient
+                          applied in real space inside the readout, which equals the k-space
+                          kernel D(k) exactly.  bit 3 (PM_FLAG_KSPACE_GRADIENT): multiply by
+                          -i D(k_j) in k-space instead and run three inverse transforms (bit 0,
+                          PM_FLAG_TWO_MESH: one component at a time in two meshes, always so
+                          for nmesh = 2048); bit 1 (PM_FLAG_SPECTRAL_KERNEL): deconvolved
+                          spectral kernel (k-space gradient k_j, W^-2), implies the k-space
+                          path; bit 2 (PM_FLAG_MLP_TENSOR): the learned factor's table on the
+                          tensor cores (BF16 operands, FP32 accumulation) instead of FP32;
+                          other bits 0 */
   int32_t pad1;
 } pm_config;
 

@@ -128,24 +128,50 @@ int sort_into_scratch(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
   return sort_particles(c, u, n, s);
 }
 
+// Where the force at the sorted scratch particles goes: with perm, F_out[d n + perm[i]]
+// (f_out); else p_out = ps + K F and f_out = F in sorted order, u_out / id_out (when
+// set) receive the sorted positions and ids.
+struct ForceOut {
+  const float* ps;
+  float K;
+  float* p_out;
+  float* f_out;
+  uint32_t* u_out;
+  uint32_t* id_out;
+  const uint32_t* perm;
+};
+
+// The real-space gradient (one potential mesh) unless the k-space form is asked for.
+bool stencil_force(const pm_ctx* c) {
+  return (c->cfg.flags & (PM_FLAG_SPECTRAL_KERNEL | PM_FLAG_KSPACE_GRADIENT)) == 0;
+}
+
 // Paint of the sorted scratch particles into meshA (padded), then the force at every
-// sorted particle.  With the third mesh: the fused x pass gives all three component
-// meshes and one readout reads them (per_all); without it, one component mesh at a
-// time in meshA (per_comp).
-template <class F1, class F3>
-int force_components(pm_ctx* c, int64_t n, double a, cudaStream_t s, F1&& per_comp, F3&& per_all) {
+// sorted particle.  Default: the potential in meshA and the stencil readout.  k-space
+// gradient with the third mesh: the fused x pass gives all three component meshes and
+// one readout reads them; without it, one component mesh at a time in meshA.
+int force_components(pm_ctx* c, int64_t n, double a, const ForceOut& o, cudaStream_t s) {
   float* realA = reinterpret_cast<float*>(c->meshA);
+  const int rp = 2 * c->g.pc;
   mlp_table(c, a, s);
-  paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, 2 * c->g.pc, s);
+  paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s);
+  if (stencil_force(c)) {
+    fft_potential(c, c->g, c->meshA, s);
+    readout_fd4_kick(c, c->us, o.ps, c->ids, n, realA, rp, o.K, o.p_out, o.f_out, o.u_out, o.id_out, o.perm,
+                     s);
+    return PM_OK;
+  }
   if (c->meshC) {
     fft_force_fused(c, c->g, c->meshA, c->meshB, c->meshC, s);
-    per_all(realA, reinterpret_cast<float*>(c->meshB), reinterpret_cast<float*>(c->meshC));
+    readout3_kick(c, c->us, o.ps, c->ids, n, realA, reinterpret_cast<float*>(c->meshB),
+                  reinterpret_cast<float*>(c->meshC), rp, o.K, o.p_out, o.f_out, o.u_out, o.id_out, o.perm, s);
     return PM_OK;
   }
   fft_forward(c, c->g, c->meshA, c->meshB, 1, s);
   for (int comp = 0; comp < 3; ++comp) {
     fft_inverse_component(c, c->g, c->meshB, c->meshA, comp, s);
-    per_comp(comp, realA);
+    readout_kick(c, c->us, o.ps, c->ids, n, realA, rp, comp, o.K, o.p_out, o.f_out, comp == 0 ? o.u_out : nullptr,
+                 comp == 0 ? o.id_out : nullptr, o.perm, s);
   }
   return PM_OK;
 }
@@ -171,16 +197,7 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
     rc = sort_into_scratch(c, st->u, n, s);
     if (rc != PM_OK) return rc;
     gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
-    force_components(
-        c, n, a0, s,
-        [&](int comp, float* mesh) {
-          readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, st->p, st->f,
-                       comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
-        },
-        [&](float* mx, float* my, float* mz) {
-          readout3_kick(c, c->us, c->ps, c->ids, n, mx, my, mz, 2 * c->g.pc, 0.0f, st->p, st->f,
-                        st->u, st->id, nullptr, s);
-        });
+    force_components(c, n, a0, ForceOut{c->ps, 0.0f, st->p, st->f, st->u, st->id, nullptr}, s);
     st->f_valid = 1;
   }
   // first half kick + drift + keys of the drifted positions
@@ -189,16 +206,7 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
   if (rc != PM_OK) return rc;
   gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
   // force at a1 and the second half kick, written back in tile order
-  force_components(
-      c, n, a1, s,
-      [&](int comp, float* mesh) {
-        readout_kick(c, c->us, c->ps, c->ids, n, mesh, 2 * c->g.pc, comp, (float)k[2], st->p, st->f,
-                     comp == 0 ? st->u : nullptr, comp == 0 ? st->id : nullptr, nullptr, s);
-      },
-      [&](float* mx, float* my, float* mz) {
-        readout3_kick(c, c->us, c->ps, c->ids, n, mx, my, mz, 2 * c->g.pc, (float)k[2], st->p,
-                      st->f, st->u, st->id, nullptr, s);
-      });
+  force_components(c, n, a1, ForceOut{c->ps, (float)k[2], st->p, st->f, st->u, st->id, nullptr}, s);
   st->a = a1;
   st->f_valid = 1;
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
@@ -470,16 +478,7 @@ int pm_force(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, float*
   int rc = sort_into_scratch(c, u, n, s);
   if (rc != PM_OK) return rc;
   gather_sorted(c, u, nullptr, id, n, c->vals[0], s);
-  force_components(
-      c, n, c->force_a, s,
-      [&](int comp, float* mesh) {
-        readout_kick(c, c->us, nullptr, c->ids, n, mesh, 2 * c->g.pc, comp, 0.0f, nullptr, F_out,
-                     nullptr, nullptr, c->vals[0], s);
-      },
-      [&](float* mx, float* my, float* mz) {
-        readout3_kick(c, c->us, nullptr, c->ids, n, mx, my, mz, 2 * c->g.pc, 0.0f, nullptr, F_out,
-                      nullptr, nullptr, c->vals[0], s);
-      });
+  force_components(c, n, c->force_a, ForceOut{nullptr, 0.0f, nullptr, F_out, nullptr, nullptr, c->vals[0]}, s);
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
 
@@ -817,7 +816,8 @@ const char* pm_kernel_name(int32_t k) {
       "paint_tiles",   "fft_z_r2c",    "fft_y",        "fft_x_green",     "fft_x_grad",
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
       "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
-      "readout3_kick", "adjoint",      "mlp_table",    "mlp_backward", "mlp_misc"};
+      "readout3_kick", "adjoint",      "mlp_table",    "mlp_backward", "mlp_misc",
+      "fft_x_potential", "readout_fd4_kick"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

@@ -90,7 +90,9 @@ int validate_config(const pm_config& c) {
   if (c.nsites > 0 && (c.nshell < 1 || c.nfib < 0)) return PM_EINVAL;
   if (!(c.h > 0.0) || !(c.omega_m > 0.0)) return PM_EINVAL;
   if (c.n_nu < 0 || c.n_nu > 3) return PM_EINVAL;
-  if (c.flags & ~(uint32_t)(PM_FLAG_TWO_MESH | PM_FLAG_SPECTRAL_KERNEL | PM_FLAG_MLP_TENSOR)) return PM_EINVAL;
+  if (c.flags & ~(uint32_t)(PM_FLAG_TWO_MESH | PM_FLAG_SPECTRAL_KERNEL | PM_FLAG_MLP_TENSOR |
+                           PM_FLAG_KSPACE_GRADIENT))
+    return PM_EINVAL;
   for (int i = 0; i < c.n_nu; ++i)
     if (!(c.m_nu[i] >= 0.0) || !std::isfinite(c.m_nu[i])) return PM_EINVAL;
   if (c.nsites > 0) {

@@ -161,10 +161,11 @@ __device__ __forceinline__ int nsq_index(int kx, int ky, int kz) {
   return nx * nx + ny * ny + kz * kz;
 }
 
-enum { EPI_NONE = 0, EPI_GREEN = 1 };
+enum { EPI_NONE = 0, EPI_GREEN = 1, EPI_POT = 2 };  // EPI_POT: Green's function, then inverse
 enum { PRO_NONE = 0, PRO_GRAD = 1 };
 
-enum { MODE_PLAIN = 0, MODE_GREEN = 1, MODE_GRAD = 2, MODE_FUSED = 3 };
+// MODE_POT: forward x FFT, Green's function, inverse x FFT (the potential, one output)
+enum { MODE_PLAIN = 0, MODE_GREEN = 1, MODE_GRAD = 2, MODE_FUSED = 3, MODE_POT = 4 };
 
 }  // namespace fft
 

@@ -6,7 +6,9 @@
 // c2c, x pass c2c with the Green's function multiply fused into its epilogue
 // (written to a second buffer).  Inverse for force component j: x pass with the
 // -i k_j multiply fused into its prologue (second buffer -> first), y pass, z
-// pass c2r.
+// pass c2r.  The potential (the default force path) runs five passes in place on
+// one mesh: z r2c, y, x forward + Green's function + x inverse in one kernel, y
+// inverse, z c2r.
 //
 // Each line of M points is held by M/16 threads, 16 values each (value s of
 // thread j is element j + s M/16).  Stockham stages of radix 16 (the last stage
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
     }
   }
   run_stages<M, M, 1, INV>(v, j, sm + c, TK, tw);
-  if constexpr (EPI == EPI_GREEN) {
+  if constexpr (EPI == EPI_GREEN || EPI == EPI_POT) {
     const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
     const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
@@ -148,6 +150,7 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
       v[s] = cscale(v[s], g);
     }
   }
+  if constexpr (EPI == EPI_POT) run_stages<M, M, 1, true>(v, j, sm + c, TK, tw);
   if (!ok) return;
 #pragma unroll
   for (int s = 0; s < 16; ++s) dst[base + (long long)(j + s * Q) * stride] = v[s];
@@ -308,7 +311,9 @@ void dispatch_strided(const Geom& g, const float2* src, float2* dst, int axis, c
 template <bool INV, int EPI, int PRO>
 void strided(pm_ctx* c, const Geom& g, const float2* src, float2* dst, int axis, const float2* tw,
              const KTables& kt, int comp, cudaStream_t s) {
-  const int mode = EPI == EPI_GREEN ? MODE_GREEN : (PRO == PRO_GRAD ? MODE_GRAD : MODE_PLAIN);
+  const int mode = EPI == EPI_GREEN ? MODE_GREEN
+                   : EPI == EPI_POT  ? MODE_POT
+                                     : (PRO == PRO_GRAD ? MODE_GRAD : MODE_PLAIN);
   if (strided_tma(c, g, src, dst, nullptr, nullptr, axis, INV, mode, comp, tw, kt, s) == PM_OK) return;
   dispatch_strided<INV, EPI, PRO>(g, src, dst, axis, tw, kt, comp, s);
 }
@@ -400,6 +405,31 @@ void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz,
       LaunchScope L(c, s, K_FFT_Z_C2R);
       dispatch_z(g, bufs[comp], tw, true, s);
     }
+  }
+}
+
+void fft_potential(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s) {
+  const float2* tw = twiddles(c, g.n);
+  KTables kt = ktables(c, g);
+  {
+    LaunchScope L(c, s, K_FFT_Z_R2C);
+    dispatch_z(g, buf, tw, false, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    strided<false, EPI_NONE, PRO_NONE>(c, g, buf, buf, 1, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_X_POT);
+    strided<false, EPI_POT, PRO_NONE>(c, g, buf, buf, 0, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Y);
+    strided<true, EPI_NONE, PRO_NONE>(c, g, buf, buf, 1, tw, kt, 0, s);
+  }
+  {
+    LaunchScope L(c, s, K_FFT_Z_C2R);
+    dispatch_z(g, buf, tw, true, s);
   }
 }
 

@@ -9,9 +9,12 @@
 // back to global memory with ordinary coalesced stores.
 //
 // Variants: plain (y or x), x with the Green's function epilogue, x with the
-// -i k_j prologue, and the fused x pass of the force (forward, Green's function,
+// -i k_j prologue, the x pass of the potential (forward, Green's function, inverse;
+// in place), and the fused x pass of the k-space force (forward, Green's function,
 // then IFFT(-i k_x phi) and IFFT(phi) scaled by -i k_y and -i k_z; phi parks in the
 // tile's own input buffer, which nothing else touches until the next prefetch).
+// In-place passes are safe: a tile's columns are read (by its CTA's prefetch) and
+// written (by the same CTA, later) by one CTA only.
 //
 // Every wait on a copy is bounded: after kSpinLimit polls the CTA records
 // PM_ETIMEOUT's bit in the error word, waits (bounded) for its other copy in
@@ -153,7 +156,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
       }
     }
     run_stages<M, M, 1, INV>(v, j, work + c, TK, tw);
-    if constexpr (MODE == MODE_GREEN || MODE == MODE_FUSED) {
+    if constexpr (MODE == MODE_GREEN || MODE == MODE_FUSED || MODE == MODE_POT) {
       const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
       const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
@@ -171,6 +174,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
         }
       }
     }
+    if constexpr (MODE == MODE_POT) run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
     if constexpr (MODE == MODE_FUSED) {
       run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
       if (ok) {
@@ -319,6 +323,7 @@ int strided_tma(pm_ctx* c, const Geom& g, const float2* src, float2* d0, float2*
   if (!inv && mode == MODE_GREEN) return dispatch<false, MODE_GREEN>(c, g, map, d0, d1, d2, axis, tw, kt, comp, s);
   if (inv && mode == MODE_GRAD) return dispatch<true, MODE_GRAD>(c, g, map, d0, d1, d2, axis, tw, kt, comp, s);
   if (!inv && mode == MODE_FUSED) return dispatch<false, MODE_FUSED>(c, g, map, d0, d1, d2, axis, tw, kt, comp, s);
+  if (!inv && mode == MODE_POT) return dispatch<false, MODE_POT>(c, g, map, d0, d1, d2, axis, tw, kt, comp, s);
   return PM_EINVAL;
 }
 

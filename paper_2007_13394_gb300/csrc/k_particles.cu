@@ -1,5 +1,6 @@
 // Particle <-> mesh kernels: deterministic tile paint, CIC readout fused with the
-// kick, the first kick fused with the drift and the next sort keys.
+// kick (of force meshes, or of the potential with the 4-point gradient applied in
+// shared memory), the first kick fused with the drift and the next sort keys.
 //
 // Paint (CIC of rho / rho_bar): one CTA per 16^3 tile.  The tile's own particles
 // are the bucket range [bstart[8 t], bstart[8 t + 8]); a particle on the tile's
@@ -27,7 +28,6 @@ namespace pmnu {
 namespace {
 
 constexpr int kPaintThreads = 256;
-constexpr int kTileCells = kTile * kTile * kTile;  // 4096
 constexpr float kFixW = 4294967296.0f;              // 2^32: signed weights
 constexpr float kUnfixW = 2.3283064365386963e-10f;  // 2^-32
 constexpr float kFixM = 16777216.0f;                // 2^24: masses
@@ -252,6 +252,131 @@ __global__ void k_readout3_kick(const uint32_t* __restrict__ us, const float* __
   }
 }
 
+// Force from the potential mesh with the 4-point gradient in real space, fused with
+// the kick.  The finite-difference gradient [8 (phi(x+H) - phi(x-H)) - (phi(x+2H) -
+// phi(x-2H))] / (12 H) has exactly the transfer function i D(k) of the k-space kernel
+// (0 on the Nyquist index), so this equals the CIC readout of IFFT(-i D(k_j) phi_k)
+// while the mesh side needs one inverse transform instead of three.
+//
+// One CTA per 16^3 tile.  The tile's potential with a halo of 2 cells below and 3
+// above along x and y, and of 4 below and 3 above along z (so that every z row splits
+// into 16-byte aligned chunks, also where it wraps), is staged in shared memory with
+// asynchronous 16-byte copies (21 x 21 x 24 floats).  Each thread then takes particles
+// of the tile's bucket range [bstart[8 t], bstart[8 t + 8]), all of whose cells lie
+// in the tile, and gathers the 56 potential values its 8 CIC corners' stencils touch;
+// the first particle's position is loaded while the copies are in flight, the next
+// one's while the current one is computed.  Differences of neighbouring values are
+// formed first, so FP32 rounding scales with the gradient, not with the potential.
+// A particle outside its tile (a bucket range that does not match the positions)
+// sets the error word's invalid-input bit.
+constexpr int kFd4Threads = 256;
+constexpr int kSpanXY = kTile + 5;                 // cells -2 .. 18 along x and y
+constexpr int kSpanZ = kTile + 8;                  // cells -4 .. 19 along z
+constexpr int kChunksZ = kSpanZ / 4;               // 16-byte chunks per staged z row
+constexpr int kStageChunks = kSpanXY * kSpanXY * kChunksZ;
+constexpr int kFd4SY = kSpanZ, kFd4SX = kSpanXY * kSpanZ;
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
+    const uint32_t* __restrict__ us, const float* __restrict__ ps, const uint32_t* __restrict__ ids,
+    int64_t n, const uint32_t* __restrict__ bstart, const float* __restrict__ phi, int nm, int shift,
+    int ntl, int row_pitch, float inv12h, float K, float* __restrict__ p_out, float* __restrict__ f_out,
+    uint32_t* __restrict__ u_out, uint32_t* __restrict__ id_out, const uint32_t* __restrict__ perm,
+    int* __restrict__ err) {
+  __shared__ __align__(16) float sp[kSpanXY * kSpanXY * kSpanZ];
+  const int t = threadIdx.x;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t lo = bstart[8 * tile], hi = bstart[8 * tile + 8];
+  if (lo == hi) return;
+  const int nt = 1 << ntl;
+  const int ox = (int)(tile >> (2 * ntl)) * kTile, oy = (int)((tile >> ntl) & (nt - 1)) * kTile,
+            oz = (int)(tile & (nt - 1)) * kTile;
+  const int wrap = nm - 1;
+  // chunk k of staged row (x, y) holds cells oz - 4 + 4k .. oz - 1 + 4k (mod N): contiguous
+  // and 16-byte aligned because N, oz and the row pitch are multiples of 4 floats
+  for (int c = t; c < kStageChunks; c += kFd4Threads) {
+    const int x = c / (kSpanXY * kChunksZ), r = c - x * (kSpanXY * kChunksZ);
+    const int y = r / kChunksZ, k = r - y * kChunksZ;
+    const int gx = (ox + x - 2) & wrap, gy = (oy + y - 2) & wrap, gz = (oz - 4 + 4 * k) & wrap;
+    cp_async16(sp + x * kFd4SX + y * kFd4SY + 4 * k, phi + ((size_t)gx * nm + gy) * (size_t)row_pitch + gz);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  uint32_t i = lo + t;
+  uint32_t ux = 0, uy = 0, uz = 0;
+  if (i < hi) {
+    ux = us[i];
+    uy = us[n + i];
+    uz = us[2 * n + i];
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const float fscale = 1.0f / (float)(1u << shift);
+  const uint32_t fmask = (1u << shift) - 1u;
+  bool bad = false;
+  for (; i < hi; i += kFd4Threads) {
+    const uint32_t inext = i + kFd4Threads;
+    uint32_t nx = 0, ny = 0, nz = 0;
+    if (inext < hi) {
+      nx = us[inext];
+      ny = us[n + inext];
+      nz = us[2 * n + inext];
+    }
+    const int lx = (int)(ux >> shift) - ox, ly = (int)(uy >> shift) - oy, lz = (int)(uz >> shift) - oz;
+    if ((unsigned)lx < (unsigned)kTile && (unsigned)ly < (unsigned)kTile && (unsigned)lz < (unsigned)kTile) {
+      const float fx = (float)(ux & fmask) * fscale, fy = (float)(uy & fmask) * fscale,
+                  fz = (float)(uz & fmask) * fscale;
+      const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+      const float* q = sp + (lx + 2) * kFd4SX + (ly + 2) * kFd4SY + (lz + 4);  // phi at the particle's cell
+      // stencil sum of one axis at the two corners 0 (weight g) and 1 (weight f) of a
+      // line through q0 with stride S: g (8 (p1 - m1) - (p2 - m2)) + f (8 (p2 - p0) - (p3 - m1))
+      auto axis_sum = [](const float* q0, int S, float g, float f) {
+        const float m2 = q0[-2 * S], m1 = q0[-S], p0 = q0[0], p1 = q0[S], p2 = q0[2 * S], p3 = q0[3 * S];
+        return g * (8.0f * (p1 - m1) - (p2 - m2)) + f * (8.0f * (p2 - p0) - (p3 - m1));
+      };
+      float Fx = 0.0f, Fy = 0.0f, Fz = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          // x lines at (y, z) = (b, a); y lines at (x, z) = (b, a); z lines at (x, y) = (b, a)
+          Fx = fmaf((b ? fy : gy) * (a ? fz : gz), axis_sum(q + b * kFd4SY + a, kFd4SX, gx, fx), Fx);
+          Fy = fmaf((b ? fx : gx) * (a ? fz : gz), axis_sum(q + b * kFd4SX + a, kFd4SY, gy, fy), Fy);
+          Fz = fmaf((b ? fx : gx) * (a ? fy : gy), axis_sum(q + b * kFd4SX + a * kFd4SY, 1, gz, fz), Fz);
+        }
+      }
+      const float F[3] = {-inv12h * Fx, -inv12h * Fy, -inv12h * Fz};
+      if (perm) {  // force in the caller's order
+        const uint32_t j = perm[i];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) f_out[(int64_t)d * n + j] = F[d];
+      } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (p_out) p_out[(int64_t)d * n + i] = ps[(int64_t)d * n + i] + K * F[d];
+          if (f_out) f_out[(int64_t)d * n + i] = F[d];
+        }
+        if (u_out) {
+          u_out[i] = ux;
+          u_out[n + i] = uy;
+          u_out[2 * n + i] = uz;
+          id_out[i] = ids[i];
+        }
+      }
+    } else {
+      bad = true;
+    }
+    ux = nx;
+    uy = ny;
+    uz = nz;
+  }
+  if (bad) atomicOr(err, 1);
+}
+
 // First half kick with the cached force, drift in fixed point, next sort key.
 __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ p,
                                   const float* __restrict__ f, int64_t n, float K1, float dscale,
@@ -332,6 +457,17 @@ void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_
   k_readout3_kick<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
       us, ps, ids, n, mx, my, mz, c->g.n, 32 - c->g.logn, row_pitch, K, p_out, f_out, u_out, id_out,
       perm_scatter);
+}
+
+void readout_fd4_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                      const float* phi, int row_pitch, float K, float* p_out, float* f_out,
+                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s) {
+  if (n == 0) return;
+  LaunchScope L(c, s, K_READOUT_FD4_KICK);
+  const float inv12h = (float)((double)c->g.n / (12.0 * c->cfg.box));
+  k_readout_fd4_kick<<<(unsigned)(c->nt * c->nt * c->nt), kFd4Threads, 0, s>>>(
+      us, ps, ids, n, c->bstart, phi, c->g.n, 32 - c->g.logn, c->ntl, row_pitch, inv12h, K, p_out, f_out,
+      u_out, id_out, perm_scatter, c->err_dev);
 }
 
 void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,

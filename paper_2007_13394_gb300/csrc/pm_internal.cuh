@@ -40,6 +40,8 @@ enum Kind {
   K_MLP_TABLE,
   K_MLP_BACKWARD,
   K_MLP_MISC,
+  K_FFT_X_POT,
+  K_READOUT_FD4_KICK,
   K_NUM_KINDS
 };
 
@@ -183,6 +185,13 @@ void fft_forward(pm_ctx* c, const Geom& g, float2* buf, float2* dst, int green, 
 void fft_inverse_component(pm_ctx* c, const Geom& g, const float2* phi, float2* buf, int comp,
                            cudaStream_t s);
 void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
+// paint mesh in buf (real) -> potential phi (real, unnormalised inverse), in place
+void fft_potential(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
+// force F = -(4-point gradient of phi) read out at the sorted particles of each tile,
+// fused with the kick; arguments as readout3_kick (phi: real mesh, row pitch row_pitch)
+void readout_fd4_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
+                      const float* phi, int row_pitch, float K, float* p_out, float* f_out,
+                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s);
 // paint mesh in a (real) -> three real force meshes in a, b, cz
 void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz, cudaStream_t s);
 void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpmnu.so")
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
 SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
 MLP_HIDDEN, MLP_NPARAM = 64, 4417
-FLAG_TWO_MESH, FLAG_SPECTRAL_KERNEL, FLAG_MLP_TENSOR = 1, 2, 4
+FLAG_TWO_MESH, FLAG_SPECTRAL_KERNEL, FLAG_MLP_TENSOR, FLAG_KSPACE_GRADIENT = 1, 2, 4, 8
 
 
 class PMError(RuntimeError):

@@ -55,7 +55,7 @@ def test_mlp_eval_and_table_match_oracle(pm):
     np.testing.assert_allclose(m, ref, rtol=0, atol=2e-6 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 8, 9], ids=["stencil", "kspace_fused_x", "kspace_per_component"])
 def test_learned_force_matches_oracle(pm, flags):
     cfg = _cfg(pm, flags=flags)
     ctx = pm.ParticleMesh(cfg)

@@ -227,11 +227,13 @@ def test_readout_matches_oracle(pm):
 
 
 # ------------------------------------------------------------------ force
-@pytest.mark.parametrize("flags", [0, 1, 2, 3], ids=["fused_x", "per_component", "fused_x_spectral",
-                                                     "per_component_spectral"])
-@pytest.mark.parametrize("size", ["cfg1", "cfg2_parity"])
+@pytest.mark.parametrize("flags", [0, 8, 9, 2, 3], ids=["stencil", "kspace_fused_x", "kspace_per_component",
+                                                        "spectral_fused_x", "spectral_per_component"])
+@pytest.mark.parametrize("size", ["mesh32", "cfg1", "cfg2_parity"])
 def test_force_relative_rms_below_1e5(pm, size, flags):
-    if size == "cfg1":
+    if size == "mesh32":  # two tiles per side: the stencil halo wraps across the whole mesh
+        cfg = make_cfg(pm, nmesh=32, nc=16, nsites=4, box=128.0, nshell=4, nfib=1, flags=flags)
+    elif size == "cfg1":
         cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3, flags=flags)
     else:
         cfg = make_cfg(pm, nmesh=256, nc=128, nsites=16, box=256.0, nshell=10, nfib=3, m_nu=(0.1 / 3,) * 3,
@@ -242,6 +244,31 @@ def test_force_relative_rms_below_1e5(pm, size, flags):
     ctx.sync()
     ref = opm.force(o["u"], o["mass"], cfg.nmesh, cfg.box, o["bg"].omega_m0,
                     kernel="spectral" if flags & 2 else "fd4")
+    rel = np.sqrt(((F - ref) ** 2).sum() / (ref ** 2).sum())
+    assert rel < 1e-5, rel
+
+
+@pytest.mark.parametrize("flags", [0, 8], ids=["stencil", "kspace_fused_x"])
+def test_force_clustered_tiles(pm, flags):
+    """Force on particles packed into a few cells on tile faces (tiles holding tens of
+    thousands of particles, runs of many CTA-strides in the stencil readout) against the
+    oracle."""
+    cfg = make_cfg(pm, nmesh=128, n_max=300000, flags=flags)
+    ctx = pm.ParticleMesh(cfg)
+    rng = np.random.default_rng(14)
+    n = 300000
+    u = inputs.uniform_positions(n, seed=15)
+    k = 2 * n // 3
+    cells = rng.integers(0, 8, size=(3, k)) * 16 + rng.integers(14, 16, size=(3, k))
+    u[:, :k] = (cells.astype(np.uint64) * (2 ** 32 // 128) + rng.integers(0, 2 ** 25, size=(3, k))).astype(np.uint32)
+    ids = np.arange(n, dtype=np.uint32) % cfg.n_cdm()
+    F = ctx.force(pm.as_u32_tensor(u), pm.as_u32_tensor(ids)).cpu().numpy().astype(np.float64)
+    ctx.sync()
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    _, _, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+    mc, _ = onu.species_masses(128, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
+                               bg.omega_nu_poisson, m_shell)
+    ref = opm.force(u, np.full(n, mc), 128, cfg.box, bg.omega_m0)
     rel = np.sqrt(((F - ref) ** 2).sum() / (ref ** 2).sum())
     assert rel < 1e-5, rel
 
@@ -258,7 +285,7 @@ def test_force_conserves_momentum(pm):
 
 
 # -------------------------------------------------------------------- step
-@pytest.mark.parametrize("flags", [0, 1], ids=["fused_x", "per_component"])
+@pytest.mark.parametrize("flags", [0, 8, 9], ids=["stencil", "kspace_fused_x", "kspace_per_component"])
 def test_step_matches_oracle(pm, flags):
     cfg = make_cfg(pm, nmesh=64, nc=32, nsites=8, box=256.0, nshell=10, nfib=3, flags=flags)
     a0, a1 = 0.05, 0.07

@@ -183,6 +183,24 @@ def test_fd4_gradient_kernel_values():
     np.testing.assert_allclose(dfull[1:n // 2], -dfull[n - 1:n // 2:-1], rtol=1e-13)
 
 
+@pytest.mark.parametrize("n", [16, 32])
+def test_fd4_kernel_is_the_real_space_stencil(n):
+    """IFFT(-i D(k_j) phi_k) = -[8 (phi(x + H) - phi(x - H)) - (phi(x + 2H) - phi(x - 2H))] / (12 H)
+    along axis j, Nyquist planes included (the 4-point stencil's transfer function is
+    i D(k), zero at k H = pi): the identity that lets the force be read out from the
+    potential mesh with the stencil applied in real space."""
+    L = 40.0
+    H = L / n
+    rng = np.random.default_rng(n)
+    phi = rng.standard_normal((n, n, n))
+    phik = np.fft.rfftn(phi) / n ** 3            # unnormalised inverse gives phi back
+    for j in range(3):
+        F = pm.force_mesh(phik, L, n, j, "fd4")
+        r = lambda s: np.roll(phi, -s, axis=j)  # noqa: E731  phi(x + s H)
+        ref = -(8.0 * (r(1) - r(-1)) - (r(2) - r(-2))) / (12.0 * H)
+        np.testing.assert_allclose(F, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
 def test_momentum_conservation_and_self_force():
     rng = np.random.default_rng(6)
     n, L = 32, 50.0
