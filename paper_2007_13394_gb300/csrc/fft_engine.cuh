@@ -145,6 +145,86 @@ __device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, i
   if constexpr (!LAST) run_stages<M, TWN, NS * R, INV>(v, j, sm, cs, tw);
 }
 
+// Twiddles a thread's stages use, held in registers.  They depend only on the thread's
+// place j in its line, so a persistent kernel loads them once and reuses them for
+// every tile.  Stage NS (radix R, B = 16 / R butterflies a thread) takes B (R - 1)
+// entries, butterfly b's factor r at offset b (R - 1) + r - 1; the first stage (NS = 1)
+// takes none.
+template <int M, int NS>
+__host__ __device__ constexpr int tw_count() {
+  constexpr int REM = M / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr int own = NS > 1 ? (16 / R) * (R - 1) : 0;
+  if constexpr (NS * R == M) {
+    return own;
+  } else {
+    return own + tw_count<M, NS * R>();
+  }
+}
+
+template <int M, int TWN, int NS, int OFF, int NTW>
+__device__ __forceinline__ void load_twiddles(float2 (&w)[NTW], int j, const float2* __restrict__ tw) {
+  constexpr int REM = M / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr int B = 16 / R;
+  constexpr int Q = M / 16;
+  if constexpr (NS > 1) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int k = (j + b * Q) & (NS - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) w[OFF + b * (R - 1) + r - 1] = __ldg(tw + ((k * r * (TWN / (NS * R))) & (TWN - 1)));
+    }
+  }
+  if constexpr (NS * R < M) load_twiddles<M, TWN, NS * R, OFF + (NS > 1 ? B * (R - 1) : 0), NTW>(w, j, tw);
+}
+
+// One Stockham stage with the twiddles from registers (see stage()).
+template <int M, int NS, int R, bool INV, bool LAST, int OFF, int NTW>
+__device__ __forceinline__ void stage_reg(float2 (&v)[16], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
+  constexpr int B = 16 / R;
+  constexpr int Q = M / 16;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int jj = j + b * Q;
+    const int k = jj & (NS - 1);
+    float2 x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r] = v[b + r * B];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 t = w[OFF + b * (R - 1) + r - 1];
+        x[r] = cmul(x[r], INV ? cconj(t) : t);
+      }
+    }
+    dft<R, INV>(x);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b + r * B] = x[r];
+    } else {
+      const int base = (jj / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    __syncthreads();
+  }
+}
+
+template <int M, int NS, bool INV, int OFF, int NTW>
+__device__ __forceinline__ void run_stages_reg(float2 (&v)[16], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
+  constexpr int REM = M / NS;
+  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr bool LAST = (NS * R == M);
+  stage_reg<M, NS, R, INV, LAST, OFF, NTW>(v, j, sm, cs, w);
+  if constexpr (!LAST) run_stages_reg<M, NS * R, INV, OFF + (NS > 1 ? (16 / R) * (R - 1) : 0), NTW>(v, j, sm, cs, w);
+}
+
 // Fused epilogue / prologue of the x pass.
 struct KTables {
   const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)

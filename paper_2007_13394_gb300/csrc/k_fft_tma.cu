@@ -2,9 +2,9 @@
 //
 // A persistent CTA walks its share of the column tiles (TK adjacent kz columns of
 // one y plane or one x line set).  One thread issues the tensor-memory-accelerator
-// copies (cp.async.bulk.tensor.3d) of the NEXT tile into the second shared-memory
-// buffer while the whole CTA transforms the current one, so DRAM stays busy during
-// the radix stages.  The tile arrives dense, element (column c, line index i) at
+// copies (cp.async.bulk.tensor.3d) of the tiles one and two ahead (one ahead in the
+// two-transform passes) into further shared-memory buffers while the whole CTA
+// transforms the current one, so DRAM stays busy during the radix stages.  The tile arrives dense, element (column c, line index i) at
 // i * TK + c, which is exactly what the first Stockham stage reads.  Results go
 // back to global memory with ordinary coalesced stores.
 //
@@ -74,32 +74,43 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <int LOGM, int TK>
+// Shared memory.  Single-transform passes (plain, Green's function, gradient): three
+// tile buffers (copies run two tiles ahead of the transform), each sized for the
+// padded work layout (rounded up to 128 bytes, the alignment of a tensor copy's
+// destination) because the Stockham stages run in the buffer of the tile just read.
+// Two-transform passes (potential, fused) keep two tile buffers and a separate work
+// area: their longer register life makes the extra barrier and the 80-register cap of
+// the in-buffer layout cost more than the deeper prefetch gains (measured).
+template <int LOGM, int TK, int MODE>
 struct TmaShape {
   static constexpr int M = 1 << LOGM;
   static constexpr int BOXR = M < 256 ? M : 256;
   static constexpr int NBOX = M / BOXR;
   static constexpr int THREADS = TK * M / 16;
   static constexpr uint32_t TILE_BYTES = (uint32_t)M * TK * 8;
-  static constexpr size_t SMEM = 2 * (size_t)M * TK * 8 + (size_t)(M + M / 16 + 1) * TK * 8;
+  static constexpr size_t WORK_BYTES = (size_t)(M + M / 16 + 1) * TK * 8;
+  static constexpr bool WORK_IN_TILE = MODE != MODE_FUSED && MODE != MODE_POT;
+  static constexpr int NBUF = WORK_IN_TILE ? 3 : 2;
+  static constexpr size_t BUF_BYTES = WORK_IN_TILE ? (WORK_BYTES + 127) / 128 * 128 : (size_t)TILE_BYTES;
+  static constexpr size_t SMEM = NBUF * BUF_BYTES + (WORK_IN_TILE ? 0 : WORK_BYTES);
 };
 
 template <int LOGM, int TK, bool INV, int MODE>
-__global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_tma(
+__global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_strided_tma(
     const __grid_constant__ CUtensorMap map, float2* __restrict__ d0, float2* __restrict__ d1,
     float2* __restrict__ d2, int axis, int pc, int ntiles_z, int ntiles,
     const float2* __restrict__ tw, KTables kt, int comp, int* __restrict__ err) {
-  using S = TmaShape<LOGM, TK>;
-  constexpr int M = S::M, Q = M / 16;
+  using S = TmaShape<LOGM, TK, MODE>;
+  constexpr int M = S::M, Q = M / 16, NBUF = S::NBUF;
   extern __shared__ __align__(128) unsigned char smraw[];
-  float2* inb[2] = {reinterpret_cast<float2*>(smraw), reinterpret_cast<float2*>(smraw) + M * TK};
-  float2* work = inb[1] + M * TK;
-  __shared__ __align__(8) uint64_t bars[2];
+  auto buf = [&](int b) { return reinterpret_cast<float2*>(smraw + (size_t)b * S::BUF_BYTES); };
+  float2* const work_sep = reinterpret_cast<float2*>(smraw + NBUF * S::BUF_BYTES);
+  __shared__ __align__(8) uint64_t bars[NBUF];
   __shared__ int fail;
   const int c = threadIdx.x % TK, j = threadIdx.x / TK;
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     fail = 0;
   }
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
     mbar_expect_tx(&bars[b], S::TILE_BYTES);
 #pragma unroll
     for (int q = 0; q < S::NBOX; ++q) {
-      float2* dst = inb[b] + q * S::BOXR * TK;
+      float2* dst = buf(b) + q * S::BOXR * TK;
       if (axis == 1)
         tma_load_3d(dst, &map, kz0, q * S::BOXR, outer, &bars[b]);
       else
@@ -117,16 +128,23 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
     }
   };
   const long long stride = axis == 1 ? (long long)pc : (long long)M * pc;
-  uint32_t parity[2] = {0u, 0u};
+  constexpr int NTW = tw_count<M, 1>();
+  float2 twr[NTW];  // this thread's twiddles, for every tile of the walk
+  load_twiddles<M, M, 1, 0, NTW>(twr, j, tw);
+  uint32_t parity[NBUF];
+#pragma unroll
+  for (int b = 0; b < NBUF; ++b) parity[b] = 0u;
   int tile = blockIdx.x;
-  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NBUF - 1; ++q)
+      if (tile + q * (int)gridDim.x < ntiles) issue(tile + q * (int)gridDim.x, q);
+  }
   for (int it = 0; tile < ntiles; tile += gridDim.x, ++it) {
-    const int b = it & 1;
-    const int next = tile + gridDim.x;
-    const bool prefetched = next < ntiles;
-    if (threadIdx.x == 0 && prefetched) {
+    const int b = it % NBUF;
+    const int ahead = tile + (NBUF - 1) * (int)gridDim.x;
+    if (threadIdx.x == 0 && ahead < ntiles) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(next, b ^ 1);
+      issue(ahead, (it + NBUF - 1) % NBUF);  // the buffer released at the end of the last iteration
     }
     if (!mbar_wait_bounded(&bars[b], parity[b])) fail = 1;
     parity[b] ^= 1u;
@@ -134,7 +152,8 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
     if (fail) {
       if (threadIdx.x == 0) {
         atomicOr(err, 2);
-        if (prefetched) mbar_wait_bounded(&bars[b ^ 1], parity[b ^ 1]);
+        for (int q = 1; q < NBUF; ++q)  // copies still in flight: wait for them (bounded)
+          if (tile + q * (int)gridDim.x < ntiles) mbar_wait_bounded(&bars[(it + q) % NBUF], parity[(it + q) % NBUF]);
       }
       return;
     }
@@ -142,10 +161,12 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
     const int kz = (tile % ntiles_z) * TK + c;
     const bool ok = kz <= M / 2;
     const long long base = (axis == 1 ? (long long)outer * M * pc : (long long)outer * pc) + kz;
-    float2* in = inb[b];
+    float2* in = buf(b);
+    float2* const work = S::WORK_IN_TILE ? in : work_sep;
     float2 v[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) v[s] = in[(j + s * Q) * TK + c];
+    if constexpr (S::WORK_IN_TILE) __syncthreads();  // every input read before the stages overwrite it
     if constexpr (MODE == MODE_GRAD) {  // v *= -i k_comp; x pass: element index kx, outer ky
 #pragma unroll
       for (int s = 0; s < 16; ++s) {
@@ -155,7 +176,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
         v[s] = make_float2(kk * v[s].y, -kk * v[s].x);
       }
     }
-    run_stages<M, M, 1, INV>(v, j, work + c, TK, tw);
+    run_stages_reg<M, 1, INV, 0, NTW>(v, j, work + c, TK, twr);
     if constexpr (MODE == MODE_GREEN || MODE == MODE_FUSED || MODE == MODE_POT) {
       const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
       const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
@@ -174,16 +195,16 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
         }
       }
     }
-    if constexpr (MODE == MODE_POT) run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
+    if constexpr (MODE == MODE_POT) run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
     if constexpr (MODE == MODE_FUSED) {
-      run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
+      run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
       if (ok) {
 #pragma unroll
         for (int s = 0; s < 16; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
       }
 #pragma unroll
       for (int s = 0; s < 16; ++s) v[s] = in[(j + s * Q) * TK + c];
-      run_stages<M, M, 1, true>(v, j, work + c, TK, tw);
+      run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
       if (ok) {
         const float ky0 = __ldg(kt.kvec0 + outer), kz0 = __ldg(kt.kvec0 + kz);
 #pragma unroll
@@ -199,7 +220,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK>::THREADS, 2) k_fft_strided_
         for (int s = 0; s < 16; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
       }
     }
-    __syncthreads();  // this tile's buffer is free for the prefetch issued next iteration
+    __syncthreads();  // this tile's buffer is free for the copy issued next iteration
   }
 }
 
@@ -213,7 +234,7 @@ template <int LOGM, bool INV, int MODE>
 int launch(pm_ctx* c, const CUtensorMap* map, float2* d0, float2* d1, float2* d2, int axis, int pc,
            const float2* tw, const KTables& kt, int comp, cudaStream_t s) {
   constexpr int TK = tk_tma<LOGM>();
-  using SH = TmaShape<LOGM, TK>;
+  using SH = TmaShape<LOGM, TK, MODE>;
   constexpr int M = SH::M;
   auto kern = k_fft_strided_tma<LOGM, TK, INV, MODE>;
   static int blocks_per_sm = 0;
