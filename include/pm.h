@@ -375,6 +375,12 @@ int pm_profile_enable(pm_ctx* ctx, int32_t mask);
 int pm_profile_read(pm_ctx* ctx, int32_t kind, double* ms, int64_t* launches, int32_t reset);
 int32_t pm_kernel_kinds(void);
 const char* pm_kernel_name(int32_t kind);
+/* How pm_step re-sorted the drifted particles (out: 3 int64, host): out[0] steps that
+ * used the near-sorted re-sort (the state in the order the context's last step left
+ * it: most particles keep their key, only the others are radix-sorted), out[1] steps
+ * that sorted from scratch, out[2] the particles the last near-sorted re-sort moved
+ * between keys.  Both ways give the same stable permutation of the keys. */
+int pm_sort_stats(pm_ctx* ctx, int64_t* out);
 
 #ifdef __cplusplus
 }

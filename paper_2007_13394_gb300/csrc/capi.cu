@@ -99,6 +99,12 @@ void free_all(pm_ctx* c) {
   cudaFree(c->ids);
   cudaFree(c->counts);
   cudaFree(c->bstart);
+  cudaFree(c->bprev);
+  cudaFree(c->rs_low);
+  cudaFree(c->rs_k2);
+  cudaFree(c->rs_v2);
+  cudaFree(c->rs_dev);
+  if (c->rs_host) cudaFreeHost(c->rs_host);
   cudaFree(c->hist);
   cudaFree(c->hist_scan);
   cudaFree(c->scan_tmp);
@@ -199,14 +205,30 @@ int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStre
     gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
     force_components(c, n, a0, ForceOut{c->ps, 0.0f, st->p, st->f, st->u, st->id, nullptr}, s);
     st->f_valid = 1;
+    std::swap(c->bstart, c->bprev);  // the state is now in this sort's order
+    c->rs_n = n;
   }
-  // first half kick + drift + keys of the drifted positions
-  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale, s);
-  rc = radix_and_buckets(c, n, s);
-  if (rc != PM_OK) return rc;
-  gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+  // first half kick + drift + keys of the drifted positions; when the state is in the
+  // order of the last sort, the near-sorted re-sort, else the radix sort from scratch
+  const bool resort = n > 0 && c->rs_n == n;
+  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale, s, resort);
+  int done = 0;
+  if (resort) {
+    done = resort_near_sorted(c, st->u, st->p, st->id, n, s);
+    if (done < 0) return done;
+  }
+  if (done) {
+    ++c->rs_fast;
+  } else {
+    ++c->rs_full;
+    rc = radix_and_buckets(c, n, s);
+    if (rc != PM_OK) return rc;
+    gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+  }
   // force at a1 and the second half kick, written back in tile order
   force_components(c, n, a1, ForceOut{c->ps, (float)k[2], st->p, st->f, st->u, st->id, nullptr}, s);
+  std::swap(c->bstart, c->bprev);
+  c->rs_n = n;
   st->a = a1;
   st->f_valid = 1;
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
@@ -340,7 +362,7 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
   const int64_t nm = std::max<int64_t>(c->n_max, 1);
   const long long hb = (nm + 4095) / 4096;
   c->hist_blocks_max = hb;
-  const long long scan_n = std::max<long long>(512 * hb, c->nbuckets + 1);
+  const long long scan_n = std::max<long long>(512 * hb, 3 * (c->nbuckets + 1));
   {  // every level of the recursive scan keeps 2 * blocks words
     size_t need = 64;
     for (long long m = scan_n; m > 1; m = (m + 4095) / 4096) need += 2 * (size_t)((m + 4095) / 4096);
@@ -354,7 +376,9 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
       dalloc(&c->winv, N) || dalloc(&c->wforce, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
       dalloc(&c->keys[1], nm) || dalloc(&c->vals[0], nm) || dalloc(&c->vals[1], nm) ||
       dalloc(&c->us, 3 * nm) || dalloc(&c->ps, 3 * nm) || dalloc(&c->ids, nm) ||
-      dalloc(&c->counts, c->nbuckets + 1) || dalloc(&c->bstart, c->nbuckets + 1) ||
+      dalloc(&c->counts, 3 * (c->nbuckets + 1)) || dalloc(&c->bstart, 3 * (c->nbuckets + 1)) ||
+      dalloc(&c->bprev, 3 * (c->nbuckets + 1)) || dalloc(&c->rs_low, c->nbuckets + 1) ||
+      dalloc(&c->rs_k2, nm) || dalloc(&c->rs_v2, nm) || dalloc(&c->rs_dev, 1) ||
       dalloc(&c->hist, 512 * hb) || dalloc(&c->hist_scan, 512 * hb) ||
       dalloc(&c->scan_tmp, c->scan_tmp_elems) || dalloc(&c->pk_partial, (size_t)N * 3 * 2048) ||
       dalloc(&c->pk_final, 3 * 2048) || dalloc(&c->err_dev, 1)) {
@@ -362,7 +386,8 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
     delete c;
     return PM_ENOMEM;
   }
-  if (cudaMallocHost(&c->err_host, sizeof(int)) != cudaSuccess) {
+  if (cudaMallocHost(&c->err_host, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->rs_host, 3 * sizeof(uint32_t)) != cudaSuccess) {
     free_all(c);
     delete c;
     return PM_ENOMEM;
@@ -808,6 +833,15 @@ int pm_profile_read(pm_ctx* c, int32_t kind, double* ms, int64_t* launches, int3
   return PM_OK;
 }
 
+int pm_sort_stats(pm_ctx* c, int64_t* out) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (!out) return PM_EINVAL;
+  out[0] = c->rs_fast;
+  out[1] = c->rs_full;
+  out[2] = c->rs_last_movers;
+  return PM_OK;
+}
+
 int32_t pm_kernel_kinds(void) { return K_NUM_KINDS; }
 
 const char* pm_kernel_name(int32_t k) {
@@ -817,7 +851,7 @@ const char* pm_kernel_name(int32_t k) {
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
       "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
       "readout3_kick", "adjoint",      "mlp_table",    "mlp_backward", "mlp_misc",
-      "fft_x_potential", "readout_fd4_kick"};
+      "fft_x_potential", "readout_fd4_kick", "resort_place", "resort_misc"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

@@ -378,15 +378,25 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
 }
 
 // First half kick with the cached force, drift in fixed point, next sort key.
+// RESORT (the state is in the tile order of the last step, whose bucket starts are
+// bprev): also classify each particle for the near-sorted re-sort of k_sort.cu.  A
+// stayer keeps its key ko; every other particle is a mover.  Counts (cnt3 holds three
+// arrays of nbuckets + 1): cnt3[0][kn] all particles of new key kn, cnt3[1][kn]
+// stayers, cnt3[2][ko] movers out of old key ko; low[kn] movers from a lower old key.
+// Flag bit 1: a particle outside its old key's range [bprev[ko], bprev[ko + 1]) (the
+// state is not in bprev's order: the caller sorts from scratch).
+template <bool RESORT>
 __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ p,
                                   const float* __restrict__ f, int64_t n, float K1, float dscale,
                                   int shift, int ntl, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ counts) {
+                                  uint32_t* __restrict__ cnt3, long long nb1, const uint32_t* __restrict__ bprev,
+                                  uint32_t* __restrict__ low, uint32_t* __restrict__ flags) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = i < n;
-  uint32_t key = 0xffffffffu;
+  uint32_t key = 0xffffffffu, cat = 0xffffffffu, ko = 0xffffffffu;
+  uint32_t flag = 0u;
   if (ok) {
-    uint32_t uu[3];
+    uint32_t uu[3], u0[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       float pv = p[d * n + i] + K1 * f[d * n + i];
@@ -396,17 +406,52 @@ __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ 
       const float x = dscale * pv;
       const uint32_t step = fabsf(x) < 2147483648.0f ? (uint32_t)__float2int_rn(x)
                                                      : (uint32_t)(unsigned long long)__float2ll_rn(x);
-      uu[d] = u[d * n + i] + step;
+      u0[d] = u[d * n + i];
+      uu[d] = u0[d] + step;
       u[d * n + i] = uu[d];
     }
     key = tile_key(uu[0], uu[1], uu[2], shift, ntl);
     keys[i] = key;
+    if constexpr (RESORT) {
+      const uint32_t k0 = tile_key(u0[0], u0[1], u0[2], shift, ntl);
+      const bool in_range = (uint32_t)i >= bprev[k0] && (uint32_t)i < bprev[k0 + 1];
+      if (!in_range) {
+        flag = 1u;
+      } else if (k0 == key) {
+        cat = key << 1;  // stayer
+      } else {
+        ko = k0;
+        if (k0 < key) cat = (key << 1) | 1u;  // mover from a lower key
+      }
+    }
   }
   unsigned act = __ballot_sync(0xffffffffu, ok);
   if (ok) {
     unsigned peers = __match_any_sync(act, key);
     int leader = __ffs(peers) - 1;
-    if ((int)(threadIdx.x & 31) == leader) atomicAdd(counts + key, (uint32_t)__popc(peers));
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(cnt3 + key, (uint32_t)__popc(peers));
+  }
+  if constexpr (RESORT) {
+    const int lane = threadIdx.x & 31;
+    const unsigned has = __ballot_sync(0xffffffffu, cat != 0xffffffffu);
+    if (cat != 0xffffffffu) {
+      const unsigned peers = __match_any_sync(has, cat);
+      if (lane == __ffs(peers) - 1) {
+        if (cat & 1u)
+          atomicAdd(low + (cat >> 1), (uint32_t)__popc(peers));
+        else
+          atomicAdd(cnt3 + nb1 + (cat >> 1), (uint32_t)__popc(peers));
+      }
+    }
+    const unsigned hasm = __ballot_sync(0xffffffffu, ko != 0xffffffffu);
+    if (ko != 0xffffffffu) {
+      const unsigned peers = __match_any_sync(hasm, ko);
+      if (lane == __ffs(peers) - 1) atomicAdd(cnt3 + 2 * nb1 + ko, (uint32_t)__popc(peers));
+    }
+    unsigned fl = flag;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    if (fl && lane == 0) atomicOr(flags, fl);
   }
 }
 
@@ -471,12 +516,22 @@ void readout_fd4_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint
 }
 
 void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,
-                     float dscale, cudaStream_t s) {
-  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (c->nbuckets + 1), s);
+                     float dscale, cudaStream_t s, bool resort) {
+  const long long nb1 = c->nbuckets + 1;
+  cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * (resort ? 3 * nb1 : nb1), s);
+  if (resort) {
+    cudaMemsetAsync(c->rs_low, 0, sizeof(uint32_t) * nb1, s);
+    cudaMemsetAsync(c->rs_dev, 0, sizeof(uint32_t), s);
+  }
   if (n == 0) return;
   LaunchScope L(c, s, K_KICK_DRIFT_KEYS);
-  k_kick_drift_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-      u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0], c->counts);
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  if (resort)
+    k_kick_drift_keys<true><<<grid, 256, 0, s>>>(u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0],
+                                                  c->counts, nb1, c->bprev, c->rs_low, c->rs_dev);
+  else
+    k_kick_drift_keys<false><<<grid, 256, 0, s>>>(u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0],
+                                                   c->counts, nb1, nullptr, nullptr, nullptr);
 }
 
 void repack_real(pm_ctx* c, const Geom& g, const float* src, int sp, float* dst, int dp,

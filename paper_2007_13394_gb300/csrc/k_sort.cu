@@ -10,6 +10,16 @@
 // its block (warp match inside a round, warp-private digit counters across the
 // warp's contiguous 512 keys, one block scan over (digit, warp)) and writes it
 // through shared memory so that global writes stay coalesced.
+//
+// Near-sorted re-sort (pm_step): the state is in the order of the last step's sort,
+// bucket starts bprev, and most particles keep their key.  A stayer (same key, inside
+// its old key's range) keeps its relative order; movers are compacted in index order
+// and radix-sorted alone.  Old ranges are ordered by key, so among the particles of new
+// key B those with index below bprev[B] are exactly the movers from lower keys, those
+// inside B's old range are B's stayers, the rest came from higher keys: bucket B is
+// [lower movers | stayers | higher movers], which is the stable order.  The result is
+// the same permutation as the radix sort from scratch; a particle outside its old
+// key's range (a state not in bprev's order) sends the caller to that sort.
 #include <cuda_runtime.h>
 
 #include "pm_internal.cuh"
@@ -254,6 +264,136 @@ __global__ void k_gather(const uint32_t* __restrict__ u, const float* __restrict
   ids[k] = id ? id[i] : i;
 }
 
+// ------------------------------------------------------------------ near-sorted re-sort
+__device__ __forceinline__ void copy_particle(const uint32_t* __restrict__ u, const float* __restrict__ p,
+                                              const uint32_t* __restrict__ id, int64_t n, uint32_t i,
+                                              uint32_t dst, uint32_t* __restrict__ us, float* __restrict__ ps,
+                                              uint32_t* __restrict__ ids) {
+  us[dst] = u[i];
+  us[n + dst] = u[n + i];
+  us[2 * n + dst] = u[2 * n + i];
+  if (p) {
+    ps[dst] = p[i];
+    ps[n + dst] = p[n + i];
+    ps[2 * n + dst] = p[2 * n + i];
+  }
+  ids[dst] = id ? id[i] : i;
+}
+
+// One CTA per old tile O: walks O's range [bprev[8 O], bprev[8 O + 8]) in chunks of the
+// block size, in index order.  A block scan of the mover flags gives every particle the
+// number of movers of its own old key before it (mrank); a stayer goes to
+// bstart[B] + low[B] + (i - bprev[B]) - mrank, a mover's (new key, index) to its old
+// key's slot of the mover list, mstart3[ko] - base3 + mrank (movers in index order).
+constexpr int kResortThreads = 256;
+
+__global__ void __launch_bounds__(kResortThreads) k_resort_old_tiles(
+    const uint32_t* __restrict__ u, const float* __restrict__ p, const uint32_t* __restrict__ id, int64_t n,
+    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ bprev, const uint32_t* __restrict__ bstart3,
+    long long nb1, const uint32_t* __restrict__ low, uint32_t* __restrict__ us, float* __restrict__ ps,
+    uint32_t* __restrict__ ids, uint32_t* __restrict__ mk, uint32_t* __restrict__ mv, int64_t nm,
+    int* __restrict__ err) {
+  constexpr int W = kResortThreads / 32;
+  __shared__ uint32_t cls_lo[9];   // bprev[8 O + c]
+  __shared__ uint32_t cls_m0[8];   // movers of the tile before class c's first particle
+  __shared__ uint32_t wsum[W];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const uint32_t O = blockIdx.x;
+  if (t < 9) cls_lo[t] = bprev[8 * O + t];
+  __syncthreads();
+  const uint32_t lo = cls_lo[0], hi = cls_lo[8];
+  if (lo == hi) return;
+  const uint32_t base3 = bstart3[2 * nb1];  // n + all stayers: offset of the third scan
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t run = 0;  // movers of the tile before this chunk
+  for (uint32_t chunk = lo; chunk < hi; chunk += kResortThreads) {
+    const uint32_t i = chunk + t;
+    const bool ok = i < hi;
+    uint32_t kn = 0, c = 0;
+    uint32_t pu[3] = {0u, 0u, 0u}, pid = 0u;
+    float pp[3] = {0.f, 0.f, 0.f};
+    if (ok) {  // the particle's data is loaded before the block scan, not after it
+      kn = keys[i];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        pu[d] = u[d * n + i];
+        if (p) pp[d] = p[d * n + i];
+      }
+      pid = id ? id[i] : i;
+#pragma unroll
+      for (int k = 1; k < 8; ++k) c += i >= cls_lo[k] ? 1u : 0u;
+    }
+    const uint32_t ko = 8 * O + c;
+    const bool mover = ok && kn != ko;
+    // where the particle's run starts: B's stayers, or old key ko's slot of the mover list
+    const uint32_t run0 = !ok ? 0u : (mover ? bstart3[2 * nb1 + ko] - base3 : bstart3[ko] + low[ko]);
+    const unsigned bal = __ballot_sync(0xffffffffu, mover);
+    if (lane == 0) wsum[w] = (uint32_t)__popc(bal);
+    __syncthreads();
+    uint32_t before = run, total = 0;
+#pragma unroll
+    for (int ww = 0; ww < W; ++ww) {
+      before += ww < w ? wsum[ww] : 0u;
+      total += wsum[ww];
+    }
+    const uint32_t mex = before + (uint32_t)__popc(bal & lt);  // movers of the tile before i
+    if (ok && i == cls_lo[c]) cls_m0[c] = mex;                   // class c starts here
+    __syncthreads();
+    if (ok) {
+      const uint32_t mrank = mex - cls_m0[c];
+      if (!mover) {
+        const uint32_t dst = run0 + (i - cls_lo[c]) - mrank;
+        if (dst < (uint64_t)n) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            us[d * n + dst] = pu[d];
+            if (p) ps[d * n + dst] = pp[d];
+          }
+          ids[dst] = pid;
+        } else {
+          atomicOr(err, 1);  // inconsistent counts: never written out of range
+        }
+      } else {
+        const uint32_t pos = run0 + mrank;
+        if (pos < (uint64_t)nm) {
+          mk[pos] = kn;
+          mv[pos] = i;
+        } else {
+          atomicOr(err, 1);
+        }
+      }
+    }
+    run += total;
+    __syncthreads();  // wsum is rewritten by the next chunk
+  }
+}
+
+// Mover r of new key B in the movers' stable order: destination bstart[B] + r, behind B's
+// stayers when it came from a higher key (r >= low[B]).  The movers of keys below B
+// number bstart[B] - sstart[B], sstart = the stayers' scan (bstart3's second third
+// minus n).
+__global__ void k_place_movers(const uint32_t* __restrict__ mk, const uint32_t* __restrict__ mv, int64_t nm,
+                               const uint32_t* __restrict__ u, const float* __restrict__ p,
+                               const uint32_t* __restrict__ id, int64_t n, const uint32_t* __restrict__ bstart3,
+                               long long nb1, long long nbuckets, const uint32_t* __restrict__ low,
+                               uint32_t* __restrict__ us, float* __restrict__ ps, uint32_t* __restrict__ ids,
+                               int* __restrict__ err) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nm) return;
+  const uint32_t B = mk[j];
+  if (B >= (uint64_t)nbuckets || mv[j] >= (uint64_t)n) {
+    atomicOr(err, 1);
+    return;
+  }
+  const uint32_t s0 = bstart3[nb1 + B], s1 = bstart3[nb1 + B + 1];
+  const uint32_t r = (uint32_t)j - (bstart3[B] - (s0 - (uint32_t)n));
+  const uint32_t dst = bstart3[B] + r + (r >= low[B] ? s1 - s0 : 0u);
+  if (dst < (uint64_t)n)
+    copy_particle(u, p, id, n, mv[j], dst, us, ps, ids);
+  else
+    atomicOr(err, 1);
+}
+
 }  // namespace
 
 namespace {
@@ -297,12 +437,13 @@ int build_keys(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s) {
   return PM_OK;
 }
 
-int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
-  // bucket starts: exclusive scan of the nbuckets + 1 counts (last count is 0 -> total)
-  scan_exclusive(c, c->counts, c->bstart, c->nbuckets + 1, s);
-  if (n == 0) return PM_OK;
-  long long nblk = (n + kRadixTile - 1) / kRadixTile;
-  if (nblk > c->hist_blocks_max) return PM_EINVAL;
+namespace {
+// LSD radix passes of the context's digit width over n (key, value) pairs in buffer pair
+// 0 (values absent: the incoming index), pair 1 the other buffers.  Returns which pair
+// holds the result.
+int radix_passes(pm_ctx* c, uint32_t* const kb[2], uint32_t* const vb[2], bool index_vals, int64_t n,
+                 cudaStream_t s) {
+  const long long nblk = (n + kRadixTile - 1) / kRadixTile;
   int cur = 0;
   const int bits = c->radix_bits;
   for (int pass = 0; pass < c->radix_passes; ++pass) {
@@ -310,14 +451,14 @@ int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
     {
       LaunchScope L(c, s, K_RADIX_HIST);
       if (bits == 9)
-        k_radix_hist<9><<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
+        k_radix_hist<9><<<(unsigned)nblk, kRadixThreads, 0, s>>>(kb[cur], n, shift, nblk, c->hist);
       else
-        k_radix_hist<8><<<(unsigned)nblk, kRadixThreads, 0, s>>>(c->keys[cur], n, shift, nblk, c->hist);
+        k_radix_hist<8><<<(unsigned)nblk, kRadixThreads, 0, s>>>(kb[cur], n, shift, nblk, c->hist);
     }
     scan_exclusive(c, c->hist, c->hist_scan, (1LL << bits) * nblk, s);
     {
       LaunchScope L(c, s, K_RADIX_SCATTER);
-      const uint32_t* vin = pass == 0 ? nullptr : c->vals[cur];
+      const uint32_t* vin = (pass == 0 && index_vals) ? nullptr : vb[cur];
       const int dyn = 2 * kRadixTile * (int)sizeof(uint32_t);
       static bool attr = false;
       if (!attr) {
@@ -326,15 +467,26 @@ int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
         attr = true;
       }
       if (bits == 9)
-        k_radix_scatter<9><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(
-            c->keys[cur], vin, n, shift, nblk, c->hist, c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
+        k_radix_scatter<9><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(kb[cur], vin, n, shift, nblk, c->hist,
+                                                                      c->hist_scan, kb[cur ^ 1], vb[cur ^ 1]);
       else
-        k_radix_scatter<8><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(
-            c->keys[cur], vin, n, shift, nblk, c->hist, c->hist_scan, c->keys[cur ^ 1], c->vals[cur ^ 1]);
+        k_radix_scatter<8><<<(unsigned)nblk, kRadixThreads, dyn, s>>>(kb[cur], vin, n, shift, nblk, c->hist,
+                                                                      c->hist_scan, kb[cur ^ 1], vb[cur ^ 1]);
     }
     cur ^= 1;
   }
-  if (cur != 0) {  // keep the result in keys[0] / vals[0]
+  return cur;
+}
+}  // namespace
+
+int radix_and_buckets(pm_ctx* c, int64_t n, cudaStream_t s) {
+  // bucket starts: exclusive scan of the nbuckets + 1 counts (last count is 0 -> total)
+  scan_exclusive(c, c->counts, c->bstart, c->nbuckets + 1, s);
+  if (n == 0) return PM_OK;
+  if ((n + kRadixTile - 1) / kRadixTile > c->hist_blocks_max) return PM_EINVAL;
+  uint32_t* const kb[2] = {c->keys[0], c->keys[1]};
+  uint32_t* const vb[2] = {c->vals[0], c->vals[1]};
+  if (radix_passes(c, kb, vb, true, n, s) != 0) {  // keep the result in keys[0] / vals[0]
     std::swap(c->keys[0], c->keys[1]);
     std::swap(c->vals[0], c->vals[1]);
   }
@@ -352,6 +504,38 @@ void gather_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t*
   if (n == 0) return;
   LaunchScope L(c, s, K_GATHER);
   k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, p, id, n, perm, c->us, c->ps, c->ids);
+}
+
+int resort_near_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t* id, int64_t n,
+                       cudaStream_t s) {
+  const long long nb1 = c->nbuckets + 1;
+  // bucket starts, stayers' and old keys' movers' starts in one scan
+  scan_exclusive(c, c->counts, c->bstart, 3 * nb1, s);
+  if (n == 0) return 1;
+  PM_CUDA_TRY(cudaMemcpyAsync(c->rs_host, c->rs_dev, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(c->rs_host + 1, c->bstart + 2 * nb1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaMemcpyAsync(c->rs_host + 2, c->bstart + 3 * nb1 - 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  PM_CUDA_TRY(cudaStreamSynchronize(s));
+  if (c->rs_host[0] & 1u) return 0;  // not the order of bprev: sort from scratch
+  const int64_t nm = (int64_t)c->rs_host[2] - (int64_t)c->rs_host[1];
+  if (nm < 0 || nm > n || (nm + kRadixTile - 1) / kRadixTile > c->hist_blocks_max) return PM_EINVAL;
+  c->rs_last_movers = nm;
+  {
+    LaunchScope L(c, s, K_RESORT_PLACE);
+    k_resort_old_tiles<<<(unsigned)((long long)c->nt * c->nt * c->nt), kResortThreads, 0, s>>>(
+        u, p, id, n, c->keys[0], c->bprev, c->bstart, nb1, c->rs_low, c->us, c->ps, c->ids, c->keys[1], c->vals[1],
+        nm, c->err_dev);
+  }
+  if (nm > 0) {
+    uint32_t* const kb[2] = {c->keys[1], c->rs_k2};
+    uint32_t* const vb[2] = {c->vals[1], c->rs_v2};
+    const int r = radix_passes(c, kb, vb, false, nm, s);
+    LaunchScope L(c, s, K_RESORT_MISC);
+    k_place_movers<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(kb[r], vb[r], nm, u, p, id, n, c->bstart, nb1,
+                                                                 c->nbuckets, c->rs_low, c->us, c->ps, c->ids,
+                                                                 c->err_dev);
+  }
+  return 1;
 }
 
 }  // namespace pmnu

@@ -42,6 +42,8 @@ enum Kind {
   K_MLP_MISC,
   K_FFT_X_POT,
   K_READOUT_FD4_KICK,
+  K_RESORT_PLACE,
+  K_RESORT_MISC,
   K_NUM_KINDS
 };
 
@@ -106,8 +108,22 @@ struct pm_ctx {
   uint32_t* us = nullptr;
   float* ps = nullptr;
   uint32_t* ids = nullptr;
-  uint32_t* counts = nullptr;   // nbuckets + 1
-  uint32_t* bstart = nullptr;   // nbuckets + 1
+  uint32_t* counts = nullptr;   // 3 (nbuckets + 1), see below
+  uint32_t* bstart = nullptr;   // 3 (nbuckets + 1)
+  // near-sorted re-sort of pm_step (k_sort.cu).  counts, bstart and bprev hold three
+  // arrays of nbuckets + 1 words each: counts = [per new key | stayers per new key |
+  // movers per old key], scanned as one array into bstart (bucket starts, then the two
+  // other scans offset by n and by n + stayers).  bprev: the same for the order the last
+  // step left its state in (valid for rs_n particles, -1: none).
+  uint32_t* bprev = nullptr;
+  int64_t rs_n = -1;
+  uint32_t* rs_low = nullptr;     // movers from a lower old key, per new key (nbuckets + 1)
+  uint32_t* rs_k2 = nullptr;      // second (key, index) buffer pair of the movers' radix
+  uint32_t* rs_v2 = nullptr;
+  uint32_t* rs_dev = nullptr;     // flag bits of k_kick_drift_keys<true>
+  uint32_t* rs_host = nullptr;    // pinned: flags, first word of the third scan, last word
+  int64_t rs_fast = 0, rs_full = 0;  // re-sorts done the near-sorted way / from scratch
+  int64_t rs_last_movers = 0;        // movers of the last near-sorted re-sort
   uint32_t* hist = nullptr;     // 256 * radix blocks, raw
   uint32_t* hist_scan = nullptr;
   uint32_t* scan_tmp = nullptr;
@@ -202,8 +218,15 @@ void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t
                   const float* mesh, int row_pitch, int comp, float K, float* p_out, float* f_out,
                   uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter,
                   cudaStream_t s);
+// resort: also classify the particles against bprev for resort_near_sorted
 void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,
-                     float dscale, cudaStream_t s);
+                     float dscale, cudaStream_t s, bool resort);
+// After kick_drift_keys(resort = true): bucket starts, and if the state was in bprev's
+// order, the sorted copies us / ps / ids of (u, p, id) with the stable order of keys[0]
+// (returns 1); returns 0 (nothing written but bstart) when the caller must sort from
+// scratch, a negative status on error.  Synchronises the stream once.
+int resort_near_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint32_t* id, int64_t n,
+                       cudaStream_t s);
 void repack_real(pm_ctx* c, const Geom& g, const float* src, int src_pitch, float* dst,
                  int dst_pitch, cudaStream_t s);
 void repack_complex(pm_ctx* c, const Geom& g, const float2* src, int src_pitch, float2* dst,

@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
         "pm_kernel_kinds": (i32, []),
         "pm_kernel_name": (ctypes.c_char_p, [i32]),
+        "pm_sort_stats": (ctypes.c_int, [vp, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -504,6 +505,13 @@ class ParticleMesh:
 
     def launch_count(self):
         return int(self.lib.pm_launch_count(self.h))
+
+    def sort_stats(self):
+        """(steps re-sorted the near-sorted way, steps sorted from scratch, movers of the last
+        near-sorted re-sort)."""
+        out = (ctypes.c_int64 * 3)()
+        _check(self.lib.pm_sort_stats(self.h, out), "pm_sort_stats")
+        return int(out[0]), int(out[1]), int(out[2])
 
     def kernel_kinds(self):
         return [self.lib.pm_kernel_name(k).decode() for k in range(self.lib.pm_kernel_kinds())]
