@@ -392,7 +392,7 @@ def run_ours(args):
                    "note": "pm_step_host: u, p, id, f copied from pinned host memory to the device, "
                            "one KDK step, copied back"}
         fft_ref = None
-        if args.config not in ("cfg3", "cfg_mid"):  # the 2048^3 / 1024^3 meshes: skipped (memory, time)
+        if not args.no_fft_reference and args.config not in ("cfg3", "cfg_mid"):  # 2048^3 / 1024^3: skipped
             fft_ref = fft_reference(ctx, cfg.nmesh)
         cpu = None
         if not args.no_cpu_baseline and world == 1 and args.config not in ("cfg3", "cfg_mid"):
@@ -439,6 +439,7 @@ def main():
     ap.add_argument("--no-nu", action="store_true",
                     help="the same workload without neutrino particles (massless neutrinos)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fft-reference", action="store_true", help="skip the FFT beside cuFFT")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
