@@ -193,6 +193,16 @@ int pm_force(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, floa
  * (u, p, f) at a1 in tile order, st->a = a1, st->f_valid = 1. */
 int pm_step(pm_ctx* ctx, pm_state* st, double a0, double ah, double a1, void* stream);
 
+/* nsteps chained KDK steps: schedule (host) holds (a0, ah, a1) per step, each step's a0
+ * equal to the previous a1 (PM_EINVAL otherwise; ah <= 0: arithmetic mean).  The result
+ * equals nsteps calls of pm_step bit for bit; on the default force path the readout
+ * that ends one step also applies the next step's first half kick and drift (FastPM's
+ * KDK with the two half kicks of a step boundary in one pass over the particles), so
+ * there is no separate kick/drift pass between steps and f is written by the last step
+ * only.  On return: as pm_step after the last step.  Stream ordered, with one host
+ * synchronisation per step (the sort's choice of method). */
+int pm_run(pm_ctx* ctx, pm_state* st, const double* schedule, int64_t nsteps, void* stream);
+
 /* pm_step on HOST arrays (u[3n], p[3n], id[n], f[3n]): copies in, steps, copies out;
  * synchronous.  *f_valid is read and updated.  Device state storage is allocated on
  * first use and kept by the context. */

@@ -145,6 +145,7 @@ struct ForceOut {
   uint32_t* u_out;
   uint32_t* id_out;
   const uint32_t* perm;
+  const DriftNext* drift = nullptr;  // stencil path only: the next step's kick and drift
 };
 
 // The real-space gradient (one potential mesh) unless the k-space form is asked for.
@@ -164,7 +165,7 @@ int force_components(pm_ctx* c, int64_t n, double a, const ForceOut& o, cudaStre
   if (stencil_force(c)) {
     fft_potential(c, c->g, c->meshA, s);
     readout_fd4_kick(c, c->us, o.ps, c->ids, n, realA, rp, o.K, o.p_out, o.f_out, o.u_out, o.id_out, o.perm,
-                     s);
+                     s, o.drift);
     return PM_OK;
   }
   if (c->meshC) {
@@ -188,48 +189,133 @@ int check_state(pm_ctx* c, const pm_state* st) {
   return PM_OK;
 }
 
-int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStream_t s) {
-  int rc = check_state(c, st);
-  if (rc != PM_OK) return rc;
-  if (!(a0 > 0.0) || !(a1 > a0) || a1 > 2.0) return PM_EINVAL;
-  if (ah <= 0.0) ah = 0.5 * (a0 + a1);
-  if (!(ah >= a0 && ah <= a1)) return PM_EINVAL;
+// Sort of the drifted state (keys and counts from kick_drift_keys or a drifting
+// readout) into the scratch copies: the near-sorted re-sort when the state is in the
+// order of the last sort, else from scratch.
+int sort_drifted(pm_ctx* c, pm_state* st, cudaStream_t s) {
   const int64_t n = st->n;
-  double k[3];
-  c->cosmo.coeffs(a0, ah, a1, k);
-  const float dscale = (float)(k[1] * 4294967296.0 / c->cfg.box);
-  if (!st->f_valid) {
-    // force at a0 on the current state (leaves the state in tile order)
-    rc = sort_into_scratch(c, st->u, n, s);
-    if (rc != PM_OK) return rc;
-    gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
-    force_components(c, n, a0, ForceOut{c->ps, 0.0f, st->p, st->f, st->u, st->id, nullptr}, s);
-    st->f_valid = 1;
-    std::swap(c->bstart, c->bprev);  // the state is now in this sort's order
-    c->rs_n = n;
-  }
-  // first half kick + drift + keys of the drifted positions; when the state is in the
-  // order of the last sort, the near-sorted re-sort, else the radix sort from scratch
-  const bool resort = n > 0 && c->rs_n == n;
-  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale, s, resort);
   int done = 0;
-  if (resort) {
+  if (n > 0 && c->rs_n == n) {
     done = resort_near_sorted(c, st->u, st->p, st->id, n, s);
     if (done < 0) return done;
   }
   if (done) {
     ++c->rs_fast;
-  } else {
-    ++c->rs_full;
-    rc = radix_and_buckets(c, n, s);
-    if (rc != PM_OK) return rc;
-    gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+    return PM_OK;
   }
+  ++c->rs_full;
+  const int rc = radix_and_buckets(c, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+  return PM_OK;
+}
+
+int check_step(double a0, double& ah, double a1) {
+  if (!(a0 > 0.0) || !(a1 > a0) || a1 > 2.0) return PM_EINVAL;
+  if (ah <= 0.0) ah = 0.5 * (a0 + a1);
+  if (!(ah >= a0 && ah <= a1)) return PM_EINVAL;
+  return PM_OK;
+}
+
+// Force at a0 on a state without a valid force cache (leaves the state in tile order).
+int first_force(pm_ctx* c, pm_state* st, double a0, cudaStream_t s) {
+  const int64_t n = st->n;
+  int rc = sort_into_scratch(c, st->u, n, s);
+  if (rc != PM_OK) return rc;
+  gather_sorted(c, st->u, st->p, st->id, n, c->vals[0], s);
+  force_components(c, n, a0, ForceOut{c->ps, 0.0f, st->p, st->f, st->u, st->id, nullptr}, s);
+  st->f_valid = 1;
+  std::swap(c->bstart, c->bprev);  // the state is now in this sort's order
+  c->rs_n = n;
+  return PM_OK;
+}
+
+int step_impl(pm_ctx* c, pm_state* st, double a0, double ah, double a1, cudaStream_t s) {
+  int rc = check_state(c, st);
+  if (rc != PM_OK) return rc;
+  rc = check_step(a0, ah, a1);
+  if (rc != PM_OK) return rc;
+  const int64_t n = st->n;
+  double k[3];
+  c->cosmo.coeffs(a0, ah, a1, k);
+  const float dscale = (float)(k[1] * 4294967296.0 / c->cfg.box);
+  if (!st->f_valid) {
+    rc = first_force(c, st, a0, s);
+    if (rc != PM_OK) return rc;
+  }
+  // first half kick + drift + keys of the drifted positions; when the state is in the
+  // order of the last sort, the near-sorted re-sort, else the radix sort from scratch
+  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale, s, n > 0 && c->rs_n == n);
+  rc = sort_drifted(c, st, s);
+  if (rc != PM_OK) return rc;
   // force at a1 and the second half kick, written back in tile order
   force_components(c, n, a1, ForceOut{c->ps, (float)k[2], st->p, st->f, st->u, st->id, nullptr}, s);
   std::swap(c->bstart, c->bprev);
   c->rs_n = n;
   st->a = a1;
+  st->f_valid = 1;
+  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+}
+
+// nsteps chained KDK steps (a0, ah, a1 per step, each a0 the previous a1).  On the
+// stencil force path the readout that ends step i also applies step i + 1's first half
+// kick and drift and writes its keys, so no separate kick/drift pass runs between the
+// steps and the force cache is written only by the last one; the state after every
+// step is the one pm_step gives, bit for bit.  Other paths loop over step_impl.
+int run_impl(pm_ctx* c, pm_state* st, const double* sched, int64_t nsteps, cudaStream_t s) {
+  int rc = check_state(c, st);
+  if (rc != PM_OK) return rc;
+  if (nsteps < 0 || (nsteps > 0 && !sched)) return PM_EINVAL;
+  std::vector<double> sc(sched, sched + 3 * nsteps);
+  for (int64_t i = 0; i < nsteps; ++i) {
+    rc = check_step(sc[3 * i], sc[3 * i + 1], sc[3 * i + 2]);
+    if (rc != PM_OK) return rc;
+    if (i > 0 && sc[3 * i] != sc[3 * i - 1]) return PM_EINVAL;
+  }
+  if (nsteps == 0) return PM_OK;
+  const int64_t n = st->n;
+  if (!stencil_force(c) || n == 0) {
+    for (int64_t i = 0; i < nsteps; ++i) {
+      rc = step_impl(c, st, sc[3 * i], sc[3 * i + 1], sc[3 * i + 2], s);
+      if (rc != PM_OK) return rc;
+    }
+    return PM_OK;
+  }
+  std::vector<double> k(3 * nsteps);
+  for (int64_t i = 0; i < nsteps; ++i) c->cosmo.coeffs(sc[3 * i], sc[3 * i + 1], sc[3 * i + 2], &k[3 * i]);
+  auto dscale = [&](int64_t i) { return (float)(k[3 * i + 1] * 4294967296.0 / c->cfg.box); };
+  if (!st->f_valid) {
+    rc = first_force(c, st, sc[0], s);
+    if (rc != PM_OK) return rc;
+  }
+  kick_drift_keys(c, st->u, st->p, st->f, n, (float)k[0], dscale(0), s, c->rs_n == n);
+  const long long nb1 = c->nbuckets + 1;
+  for (int64_t i = 0; i < nsteps; ++i) {
+    rc = sort_drifted(c, st, s);
+    if (rc != PM_OK) return rc;
+    const float K2 = (float)k[3 * i + 2];
+    if (i + 1 < nsteps) {
+      // counts of the keys the drifting readout writes (the sort above has used its own)
+      PM_CUDA_TRY(cudaMemsetAsync(c->counts, 0, sizeof(uint32_t) * 3 * nb1, s));
+      PM_CUDA_TRY(cudaMemsetAsync(c->rs_low, 0, sizeof(uint32_t) * nb1, s));
+      PM_CUDA_TRY(cudaMemsetAsync(c->rs_dev, 0, sizeof(uint32_t), s));
+      DriftNext dn;
+      dn.K1 = (float)k[3 * (i + 1)];
+      dn.dscale = dscale(i + 1);
+      dn.keys = c->keys[0];
+      dn.cnt3 = c->counts;
+      dn.nb1 = nb1;
+      dn.low = c->rs_low;
+      ForceOut o{c->ps, K2, st->p, nullptr, st->u, st->id, nullptr};
+      o.drift = &dn;
+      force_components(c, n, sc[3 * i + 2], o, s);
+    } else {
+      force_components(c, n, sc[3 * i + 2], ForceOut{c->ps, K2, st->p, st->f, st->u, st->id, nullptr}, s);
+    }
+    std::swap(c->bstart, c->bprev);
+    c->rs_n = n;
+  }
+  st->a = sc[3 * nsteps - 1];
   st->f_valid = 1;
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
@@ -510,6 +596,11 @@ int pm_force(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, float*
 int pm_step(pm_ctx* c, pm_state* st, double a0, double ah, double a1, void* stream) {
   if (!valid(c)) return PM_ENOTINIT;
   return step_impl(c, st, a0, ah, a1, S(stream));
+}
+
+int pm_run(pm_ctx* c, pm_state* st, const double* schedule, int64_t nsteps, void* stream) {
+  if (!valid(c)) return PM_ENOTINIT;
+  return run_impl(c, st, schedule, nsteps, S(stream));
 }
 
 int pm_step_host(pm_ctx* c, uint32_t* u, float* p, uint32_t* id, float* f, int64_t n,

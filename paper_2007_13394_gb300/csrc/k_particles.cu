@@ -192,7 +192,7 @@ __global__ void k_readout_kick(const uint32_t* __restrict__ us, const float* __r
     f_out[(int64_t)comp * n + j] = F;
     return;
   }
-  if (p_out) p_out[(int64_t)comp * n + i] = ps[(int64_t)comp * n + i] + K * F;
+  if (p_out) p_out[(int64_t)comp * n + i] = __fmaf_rn(K, F, ps[(int64_t)comp * n + i]);
   if (f_out) f_out[(int64_t)comp * n + i] = F;
   if (u_out) {
     u_out[i] = ux;
@@ -241,7 +241,7 @@ __global__ void k_readout3_kick(const uint32_t* __restrict__ us, const float* __
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (p_out) p_out[(int64_t)d * n + i] = ps[(int64_t)d * n + i] + K * F[d];
+    if (p_out) p_out[(int64_t)d * n + i] = __fmaf_rn(K, F[d], ps[(int64_t)d * n + i]);
     if (f_out) f_out[(int64_t)d * n + i] = F[d];
   }
   if (u_out) {
@@ -269,6 +269,50 @@ __global__ void k_readout3_kick(const uint32_t* __restrict__ us, const float* __
 // formed first, so FP32 rounding scales with the gradient, not with the potential.
 // A particle outside its tile (a bucket range that does not match the positions)
 // sets the error word's invalid-input bit.
+// The next step's first half kick and drift, fused into the readout that ends a step
+// (pm_run): p = (ps + K2 F) + K1' F, u' = u + rne(Delta' p 2^32 / L), in the operations
+// and order of the unfused path (readout, then k_kick_drift_keys), so the state is
+// bit-identical.  Writes the new key and the near-sorted re-sort's counts (the
+// particle's old key is its current bucket, so it is in range by construction).
+__device__ __forceinline__ uint32_t drift_fixed(uint32_t u, float dscale, float p) {
+  const float x = dscale * p;
+  const uint32_t step = fabsf(x) < 2147483648.0f ? (uint32_t)__float2int_rn(x)
+                                                 : (uint32_t)(unsigned long long)__float2ll_rn(x);
+  return u + step;
+}
+
+__device__ __forceinline__ void drift_next(const DriftNext& dn, const float (&F)[3], const float* __restrict__ ps,
+                                           float K2, int64_t n, uint32_t i, uint32_t ux, uint32_t uy, uint32_t uz,
+                                           int shift, int ntl, float* __restrict__ p_out, float* __restrict__ f_out,
+                                           uint32_t* __restrict__ u_out) {
+  uint32_t uu[3] = {ux, uy, uz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float p1 = __fmaf_rn(K2, F[d], ps[(int64_t)d * n + i]);
+    const float p2 = __fmaf_rn(dn.K1, F[d], p1);
+    p_out[(int64_t)d * n + i] = p2;
+    if (f_out) f_out[(int64_t)d * n + i] = F[d];
+    uu[d] = drift_fixed(uu[d], dn.dscale, p2);
+    u_out[(int64_t)d * n + i] = uu[d];
+  }
+  const uint32_t kn = tile_key(uu[0], uu[1], uu[2], shift, ntl);
+  const uint32_t ko = tile_key(ux, uy, uz, shift, ntl);
+  dn.keys[i] = kn;
+  // counts: all particles by new key, stayers by new key, movers by old key, movers from
+  // a lower key by new key (warp-aggregated over the lanes here together)
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31;
+  unsigned peers = __match_any_sync(act, kn);
+  if (lane == __ffs(peers) - 1) atomicAdd(dn.cnt3 + kn, (uint32_t)__popc(peers));
+  const uint32_t cat = kn == ko ? kn << 1 : (ko < kn ? (kn << 1) | 1u : 0xffffffffu);
+  peers = __match_any_sync(act, cat);
+  if (cat != 0xffffffffu && lane == __ffs(peers) - 1)
+    atomicAdd((cat & 1u) ? dn.low + (cat >> 1) : dn.cnt3 + dn.nb1 + (cat >> 1), (uint32_t)__popc(peers));
+  const uint32_t mo = kn != ko ? ko : 0xffffffffu;
+  peers = __match_any_sync(act, mo);
+  if (mo != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(dn.cnt3 + 2 * dn.nb1 + mo, (uint32_t)__popc(peers));
+}
+
 constexpr int kFd4Threads = 256;
 constexpr int kSpanXY = kTile + 5;                 // cells -2 .. 18 along x and y
 constexpr int kSpanZ = kTile + 8;                  // cells -4 .. 19 along z
@@ -282,12 +326,13 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
                : "memory");
 }
 
+template <bool DRIFT>
 __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
     const uint32_t* __restrict__ us, const float* __restrict__ ps, const uint32_t* __restrict__ ids,
     int64_t n, const uint32_t* __restrict__ bstart, const float* __restrict__ phi, int nm, int shift,
     int ntl, int row_pitch, float inv12h, float K, float* __restrict__ p_out, float* __restrict__ f_out,
     uint32_t* __restrict__ u_out, uint32_t* __restrict__ id_out, const uint32_t* __restrict__ perm,
-    int* __restrict__ err) {
+    int* __restrict__ err, DriftNext dn) {
   __shared__ __align__(16) float sp[kSpanXY * kSpanXY * kSpanZ];
   const int t = threadIdx.x;
   const uint32_t tile = blockIdx.x;
@@ -354,10 +399,13 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
         const uint32_t j = perm[i];
 #pragma unroll
         for (int d = 0; d < 3; ++d) f_out[(int64_t)d * n + j] = F[d];
+      } else if constexpr (DRIFT) {
+        drift_next(dn, F, ps, K, n, i, ux, uy, uz, shift, ntl, p_out, f_out, u_out);
+        id_out[i] = ids[i];
       } else {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          if (p_out) p_out[(int64_t)d * n + i] = ps[(int64_t)d * n + i] + K * F[d];
+          if (p_out) p_out[(int64_t)d * n + i] = __fmaf_rn(K, F[d], ps[(int64_t)d * n + i]);
           if (f_out) f_out[(int64_t)d * n + i] = F[d];
         }
         if (u_out) {
@@ -399,15 +447,12 @@ __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ 
     uint32_t uu[3], u0[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      float pv = p[d * n + i] + K1 * f[d * n + i];
+      const float pv = __fmaf_rn(K1, f[d * n + i], p[d * n + i]);
       p[d * n + i] = pv;
       // u += rne(Delta p 2^32 / L), modulo 2^32; the 32-bit conversion (same rounding)
       // whenever the step fits, the 64-bit one (FP64 pipe) only for steps of 2^31 or more
-      const float x = dscale * pv;
-      const uint32_t step = fabsf(x) < 2147483648.0f ? (uint32_t)__float2int_rn(x)
-                                                     : (uint32_t)(unsigned long long)__float2ll_rn(x);
       u0[d] = u[d * n + i];
-      uu[d] = u0[d] + step;
+      uu[d] = drift_fixed(u0[d], dscale, pv);
       u[d * n + i] = uu[d];
     }
     key = tile_key(uu[0], uu[1], uu[2], shift, ntl);
@@ -506,13 +551,21 @@ void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_
 
 void readout_fd4_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
                       const float* phi, int row_pitch, float K, float* p_out, float* f_out,
-                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s) {
+                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s,
+                      const DriftNext* dn) {
   if (n == 0) return;
   LaunchScope L(c, s, K_READOUT_FD4_KICK);
   const float inv12h = (float)((double)c->g.n / (12.0 * c->cfg.box));
-  k_readout_fd4_kick<<<(unsigned)(c->nt * c->nt * c->nt), kFd4Threads, 0, s>>>(
-      us, ps, ids, n, c->bstart, phi, c->g.n, 32 - c->g.logn, c->ntl, row_pitch, inv12h, K, p_out, f_out,
-      u_out, id_out, perm_scatter, c->err_dev);
+  const unsigned grid = (unsigned)(c->nt * c->nt * c->nt);
+  if (dn)
+    k_readout_fd4_kick<true><<<grid, kFd4Threads, 0, s>>>(us, ps, ids, n, c->bstart, phi, c->g.n, 32 - c->g.logn,
+                                                          c->ntl, row_pitch, inv12h, K, p_out, f_out, u_out,
+                                                          id_out, nullptr, c->err_dev, *dn);
+  else
+    k_readout_fd4_kick<false><<<grid, kFd4Threads, 0, s>>>(us, ps, ids, n, c->bstart, phi, c->g.n,
+                                                           32 - c->g.logn, c->ntl, row_pitch, inv12h, K, p_out,
+                                                           f_out, u_out, id_out, perm_scatter, c->err_dev,
+                                                           DriftNext{});
 }
 
 void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n, float K1,

@@ -60,6 +60,18 @@ struct MassTable {
   float m_nu[kMaxShell];
 };
 
+// The next step's first half kick and drift, fused into a readout (pm_run): K1 and the
+// drift's fixed-point scale, where the new keys go and the near-sorted re-sort's counts
+// (cnt3: three arrays of nb1 words, low: nb1 words).
+struct DriftNext {
+  float K1 = 0.0f;
+  float dscale = 0.0f;
+  uint32_t* keys = nullptr;
+  uint32_t* cnt3 = nullptr;
+  long long nb1 = 0;
+  uint32_t* low = nullptr;
+};
+
 // Mesh geometry for one FFT size.
 struct Geom {
   int n = 0, logn = 0;   // points per side
@@ -205,9 +217,12 @@ void fft_inverse_plain(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
 void fft_potential(pm_ctx* c, const Geom& g, float2* buf, cudaStream_t s);
 // force F = -(4-point gradient of phi) read out at the sorted particles of each tile,
 // fused with the kick; arguments as readout3_kick (phi: real mesh, row pitch row_pitch)
+// dn non-null: also the next step's first half kick, drift, keys and counts (u_out, p_out
+// and id_out required; f_out optional)
 void readout_fd4_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,
                       const float* phi, int row_pitch, float K, float* p_out, float* f_out,
-                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s);
+                      uint32_t* u_out, uint32_t* id_out, const uint32_t* perm_scatter, cudaStream_t s,
+                      const DriftNext* dn = nullptr);
 // paint mesh in a (real) -> three real force meshes in a, b, cz
 void fft_force_fused(pm_ctx* c, const Geom& g, float2* a, float2* b, float2* cz, cudaStream_t s);
 void readout3_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,

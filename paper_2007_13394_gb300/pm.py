@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_paint": (ctypes.c_int, [vp, vp, vp, i64, i32, vp, vp]),
         "pm_force": (ctypes.c_int, [vp, vp, vp, i64, vp, vp]),
         "pm_step": (ctypes.c_int, [vp, ctypes.POINTER(State), d, d, d, vp]),
+        "pm_run": (ctypes.c_int, [vp, ctypes.POINTER(State), dp, i64, vp]),
         "pm_step_host": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, ctypes.POINTER(i32), d, d, d, vp]),
         "pm_power": (ctypes.c_int, [vp, vp, vp, i64, i32, i32, i32, vp, vp, vp, vp]),
         "pm_ic": (ctypes.c_int, [vp, vp, d, d, ctypes.POINTER(State), vp]),
@@ -301,6 +302,18 @@ class ParticleMesh:
         s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
                   st["u"].shape[1], st.get("a", a0), int(st.get("f_valid", 0)), 0)
         _check(self.lib.pm_step(self.h, ctypes.byref(s), a0, ah, a1, _stream()), "pm_step")
+        st["a"], st["f_valid"] = s.a, s.f_valid
+        return st
+
+    def run(self, st: dict, steps):
+        """Chained KDK steps [(a0, ah, a1), ...] through pm_run (same result as step() per step)."""
+        steps = [tuple(float(x) for x in t) for t in steps]
+        if not steps:
+            return st
+        sched = (ctypes.c_double * (3 * len(steps)))(*[x for t in steps for x in t])
+        s = State(_ptr(st["u"]).value, _ptr(st["p"]).value, _ptr(st["id"]).value, _ptr(st["f"]).value,
+                  st["u"].shape[1], st.get("a", steps[0][0]), int(st.get("f_valid", 0)), 0)
+        _check(self.lib.pm_run(self.h, ctypes.byref(s), sched, len(steps), _stream()), "pm_run")
         st["a"], st["f_valid"] = s.a, s.f_valid
         return st
 

@@ -90,3 +90,37 @@ def test_shuffled_state_sorts_from_scratch(pm):
     u2, ids2 = _host(pm, st)
     assert np.array_equal(ids2, _expected_order(pm, ids1, u2, ids2, 64))
     assert ctx.sort_stats()[:2] == (2, 1)
+
+
+@pytest.mark.parametrize("warm", [False, True], ids=["from_ics", "after_a_step"])
+def test_run_equals_repeated_steps_bitwise(pm, warm):
+    """pm_run fuses each step's last readout with the next step's first half kick and
+    drift; the state after it must be that of pm_step called once per step, bit for bit."""
+    cfg = pm.RunConfig(box=256.0, nmesh=64, nc=32, nsites=8, nshell=10, nfib=3, m_nu=(0.1,) * 3)
+    ca, cb = pm.ParticleMesh(cfg), pm.ParticleMesh(cfg)
+    sa, sb = _state(pm, ca, cfg, seed=4), _state(pm, cb, cfg, seed=4)
+    if warm:
+        ca.step(sa, 0.05, 0.075, 0.1)
+        cb.step(sb, 0.05, 0.075, 0.1)
+        sched = [(0.1, 0.15, 0.2), (0.2, 0.3, 0.4), (0.4, 0.55, 0.7), (0.7, 0.85, 1.0)]
+    else:
+        sched = [(0.05, 0.1, 0.15), (0.15, 0.3, 0.45), (0.45, 0.7, 1.0)]
+    for t in sched:
+        ca.step(sa, *t)
+    cb.run(sb, sched)
+    ca.sync()
+    cb.sync()
+    for k in ("u", "p", "f", "id"):
+        assert torch.equal(sa[k], sb[k]), k
+    assert sb["a"] == sched[-1][2] and sb["f_valid"] == 1
+    assert cb.sort_stats()[:2] == ca.sort_stats()[:2]
+
+
+def test_run_rejects_a_broken_schedule(pm):
+    cfg = pm.RunConfig(box=256.0, nmesh=64, nc=32, nsites=8, nshell=10, nfib=3, m_nu=(0.1,) * 3)
+    ctx = pm.ParticleMesh(cfg)
+    st = _state(pm, ctx, cfg, seed=5)
+    with pytest.raises(pm.PMError):
+        ctx.run(st, [(0.05, 0.06, 0.07), (0.08, 0.09, 0.1)])  # a0 of the second != a1 of the first
+    ctx.run(st, [])
+    assert st["f_valid"] == 0
