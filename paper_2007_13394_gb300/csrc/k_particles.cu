@@ -97,12 +97,33 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
   bool bad = false;
   int r = 0;
-  for (uint32_t v = t; v < total; v += kPaintThreads) {
+  // the particle of iteration v + kPaintThreads is loaded while v's corners are added
+  auto locate = [&](uint32_t v) {
     while (v >= run_pre[r + 1]) ++r;  // v only grows, so the run index only grows
-    const uint32_t k = run_lo[r] + (v - run_pre[r]);
-    const float m = wts ? wts[k] : id_mass(mt, ids[k], species, &bad);  // weights: signed, sorted order
+    return run_lo[r] + (v - run_pre[r]);
+  };
+  uint32_t k = 0, qid = 0, qu0 = 0, qu1 = 0, qu2 = 0;
+  float qw = 0.0f;
+  if ((uint32_t)t < total) {
+    k = locate(t);
+    if (wts) qw = wts[k]; else qid = ids[k];
+    qu0 = us[k];
+    qu1 = us[n + k];
+    qu2 = us[2 * n + k];
+  }
+  for (uint32_t v = t; v < total; v += kPaintThreads) {
+    const uint32_t u0 = qu0, u1 = qu1, u2 = qu2, idv = qid;
+    const float wv = qw;
+    const uint32_t vn = v + kPaintThreads;
+    if (vn < total) {
+      const uint32_t kn = locate(vn);
+      if (wts) qw = wts[kn]; else qid = ids[kn];
+      qu0 = us[kn];
+      qu1 = us[n + kn];
+      qu2 = us[2 * n + kn];
+    }
+    const float m = wts ? wv : id_mass(mt, idv, species, &bad);  // weights: signed, sorted order
     if (m == 0.0f) continue;
-    const uint32_t u0 = us[k], u1 = us[n + k], u2 = us[2 * n + k];
     int l[3] = {(int)(u0 >> shift) - ox, (int)(u1 >> shift) - oy, (int)(u2 >> shift) - oz};
     int lo_ok = 0;  // bit d: lower corner inside along d; bit 3 + d: upper inside
 #pragma unroll
