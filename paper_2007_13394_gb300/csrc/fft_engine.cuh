@@ -1,8 +1,8 @@
 // Stockham FFT engine shared by the FFT kernels (device code only).
 //
-// A line of M points (M a power of two, 16 <= M <= 2048) is held by M/16 threads,
-// 16 values each (value s of thread j is element j + s M/16).  Stockham stages of
-// radix 16 (the last stage radix 2..16) run in registers; between stages the line
+// A line of M points (M a power of two, 16 <= M <= 2048) is held by M/V threads,
+// V = 16 (or 8) values each (value s of thread j is element j + s M/V).  Stockham
+// stages of radix V (the last stage radix 2..V) run in registers; between stages the line
 // goes through shared memory, padded by one float2 per 16 so that the stride-16
 // writes of the first stage are free of bank conflicts.  A line's elements may be
 // interleaved with other lines' (column stride cs in shared memory).  Twiddles
@@ -97,12 +97,13 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
   dft_layers<R, INV, 2>(x);
 }
 
-// One Stockham stage on a line of M points (sub-transform length NS, radix R).
-template <int M, int TWN, int NS, int R, bool INV, bool LAST>
-__device__ __forceinline__ void stage(float2 (&v)[16], int j, float2* sm, int cs,
+// One Stockham stage on a line of M points (sub-transform length NS, radix R), V values
+// a thread (value s of thread j is element j + s M / V).
+template <int M, int TWN, int NS, int R, bool INV, bool LAST, int V = 16>
+__device__ __forceinline__ void stage(float2 (&v)[V], int j, float2* sm, int cs,
                                       const float2* __restrict__ tw) {
-  constexpr int B = 16 / R;  // butterflies per thread
-  constexpr int Q = M / 16;
+  constexpr int B = V / R;  // butterflies per thread
+  constexpr int Q = M / V;
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int jj = j + b * Q;
@@ -130,44 +131,44 @@ __device__ __forceinline__ void stage(float2 (&v)[16], int j, float2* sm, int cs
   if constexpr (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    for (int s = 0; s < V; ++s) v[s] = sm[padi(j + s * Q) * cs];
     __syncthreads();
   }
 }
 
-template <int M, int TWN, int NS, bool INV>
-__device__ __forceinline__ void run_stages(float2 (&v)[16], int j, float2* sm, int cs,
+template <int M, int TWN, int NS, bool INV, int V = 16>
+__device__ __forceinline__ void run_stages(float2 (&v)[V], int j, float2* sm, int cs,
                                            const float2* __restrict__ tw) {
   constexpr int REM = M / NS;
-  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr int R = REM >= V ? V : REM;
   constexpr bool LAST = (NS * R == M);
-  stage<M, TWN, NS, R, INV, LAST>(v, j, sm, cs, tw);
-  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV>(v, j, sm, cs, tw);
+  stage<M, TWN, NS, R, INV, LAST, V>(v, j, sm, cs, tw);
+  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV, V>(v, j, sm, cs, tw);
 }
 
 // Twiddles a thread's stages use, held in registers.  They depend only on the thread's
 // place j in its line, so a persistent kernel loads them once and reuses them for
-// every tile.  Stage NS (radix R, B = 16 / R butterflies a thread) takes B (R - 1)
+// every tile.  Stage NS (radix R, B = V / R butterflies a thread) takes B (R - 1)
 // entries, butterfly b's factor r at offset b (R - 1) + r - 1; the first stage (NS = 1)
 // takes none.
-template <int M, int NS>
+template <int M, int NS, int V = 16>
 __host__ __device__ constexpr int tw_count() {
   constexpr int REM = M / NS;
-  constexpr int R = REM >= 16 ? 16 : REM;
-  constexpr int own = NS > 1 ? (16 / R) * (R - 1) : 0;
+  constexpr int R = REM >= V ? V : REM;
+  constexpr int own = NS > 1 ? (V / R) * (R - 1) : 0;
   if constexpr (NS * R == M) {
     return own;
   } else {
-    return own + tw_count<M, NS * R>();
+    return own + tw_count<M, NS * R, V>();
   }
 }
 
-template <int M, int TWN, int NS, int OFF, int NTW>
+template <int M, int TWN, int NS, int OFF, int NTW, int V = 16>
 __device__ __forceinline__ void load_twiddles(float2 (&w)[NTW], int j, const float2* __restrict__ tw) {
   constexpr int REM = M / NS;
-  constexpr int R = REM >= 16 ? 16 : REM;
-  constexpr int B = 16 / R;
-  constexpr int Q = M / 16;
+  constexpr int R = REM >= V ? V : REM;
+  constexpr int B = V / R;
+  constexpr int Q = M / V;
   if constexpr (NS > 1) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -176,14 +177,14 @@ __device__ __forceinline__ void load_twiddles(float2 (&w)[NTW], int j, const flo
       for (int r = 1; r < R; ++r) w[OFF + b * (R - 1) + r - 1] = __ldg(tw + ((k * r * (TWN / (NS * R))) & (TWN - 1)));
     }
   }
-  if constexpr (NS * R < M) load_twiddles<M, TWN, NS * R, OFF + (NS > 1 ? B * (R - 1) : 0), NTW>(w, j, tw);
+  if constexpr (NS * R < M) load_twiddles<M, TWN, NS * R, OFF + (NS > 1 ? B * (R - 1) : 0), NTW, V>(w, j, tw);
 }
 
 // One Stockham stage with the twiddles from registers (see stage()).
-template <int M, int NS, int R, bool INV, bool LAST, int OFF, int NTW>
-__device__ __forceinline__ void stage_reg(float2 (&v)[16], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
-  constexpr int B = 16 / R;
-  constexpr int Q = M / 16;
+template <int M, int NS, int R, bool INV, bool LAST, int OFF, int NTW, int V = 16>
+__device__ __forceinline__ void stage_reg(float2 (&v)[V], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
+  constexpr int B = V / R;
+  constexpr int Q = M / V;
 #pragma unroll
   for (int b = 0; b < B; ++b) {
     const int jj = j + b * Q;
@@ -211,18 +212,18 @@ __device__ __forceinline__ void stage_reg(float2 (&v)[16], int j, float2* sm, in
   if constexpr (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    for (int s = 0; s < V; ++s) v[s] = sm[padi(j + s * Q) * cs];
     __syncthreads();
   }
 }
 
-template <int M, int NS, bool INV, int OFF, int NTW>
-__device__ __forceinline__ void run_stages_reg(float2 (&v)[16], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
+template <int M, int NS, bool INV, int OFF, int NTW, int V = 16>
+__device__ __forceinline__ void run_stages_reg(float2 (&v)[V], int j, float2* sm, int cs, const float2 (&w)[NTW]) {
   constexpr int REM = M / NS;
-  constexpr int R = REM >= 16 ? 16 : REM;
+  constexpr int R = REM >= V ? V : REM;
   constexpr bool LAST = (NS * R == M);
-  stage_reg<M, NS, R, INV, LAST, OFF, NTW>(v, j, sm, cs, w);
-  if constexpr (!LAST) run_stages_reg<M, NS * R, INV, OFF + (NS > 1 ? (16 / R) * (R - 1) : 0), NTW>(v, j, sm, cs, w);
+  stage_reg<M, NS, R, INV, LAST, OFF, NTW, V>(v, j, sm, cs, w);
+  if constexpr (!LAST) run_stages_reg<M, NS * R, INV, OFF + (NS > 1 ? (V / R) * (R - 1) : 0), NTW, V>(v, j, sm, cs, w);
 }
 
 // Fused epilogue / prologue of the x pass.

@@ -81,12 +81,20 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 // Two-transform passes (potential, fused) keep two tile buffers and a separate work
 // area: their longer register life makes the extra barrier and the 80-register cap of
 // the in-buffer layout cost more than the deeper prefetch gains (measured).
+// values a thread holds: 8 (radix-8 stages, 64 registers, twice the resident warps of
+// the 16-value form) from 256-point lines up
+template <int LOGM>
+constexpr int vpt_tma() {
+  return LOGM >= 8 ? 8 : 16;
+}
+
 template <int LOGM, int TK, int MODE>
 struct TmaShape {
   static constexpr int M = 1 << LOGM;
+  static constexpr int V = vpt_tma<LOGM>();
   static constexpr int BOXR = M < 256 ? M : 256;
   static constexpr int NBOX = M / BOXR;
-  static constexpr int THREADS = TK * M / 16;
+  static constexpr int THREADS = TK * M / V;
   static constexpr uint32_t TILE_BYTES = (uint32_t)M * TK * 8;
   static constexpr size_t WORK_BYTES = (size_t)(M + M / 16 + 1) * TK * 8;
   static constexpr bool WORK_IN_TILE = MODE != MODE_FUSED && MODE != MODE_POT;
@@ -101,7 +109,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     float2* __restrict__ d2, int axis, int pc, int ntiles_z, int ntiles,
     const float2* __restrict__ tw, KTables kt, int comp, int* __restrict__ err) {
   using S = TmaShape<LOGM, TK, MODE>;
-  constexpr int M = S::M, Q = M / 16, NBUF = S::NBUF;
+  constexpr int M = S::M, V = S::V, Q = M / V, NBUF = S::NBUF;
   extern __shared__ __align__(128) unsigned char smraw[];
   auto buf = [&](int b) { return reinterpret_cast<float2*>(smraw + (size_t)b * S::BUF_BYTES); };
   float2* const work_sep = reinterpret_cast<float2*>(smraw + NBUF * S::BUF_BYTES);
@@ -128,9 +136,9 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     }
   };
   const long long stride = axis == 1 ? (long long)pc : (long long)M * pc;
-  constexpr int NTW = tw_count<M, 1>();
+  constexpr int NTW = tw_count<M, 1, V>();
   float2 twr[NTW];  // this thread's twiddles, for every tile of the walk
-  load_twiddles<M, M, 1, 0, NTW>(twr, j, tw);
+  load_twiddles<M, M, 1, 0, NTW, V>(twr, j, tw);
   uint32_t parity[NBUF];
 #pragma unroll
   for (int b = 0; b < NBUF; ++b) parity[b] = 0u;
@@ -163,25 +171,25 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     const long long base = (axis == 1 ? (long long)outer * M * pc : (long long)outer * pc) + kz;
     float2* in = buf(b);
     float2* const work = S::WORK_IN_TILE ? in : work_sep;
-    float2 v[16];
+    float2 v[V];
 #pragma unroll
-    for (int s = 0; s < 16; ++s) v[s] = in[(j + s * Q) * TK + c];
+    for (int s = 0; s < V; ++s) v[s] = in[(j + s * Q) * TK + c];
     if constexpr (S::WORK_IN_TILE) __syncthreads();  // every input read before the stages overwrite it
     if constexpr (MODE == MODE_GRAD) {  // v *= -i k_comp; x pass: element index kx, outer ky
 #pragma unroll
-      for (int s = 0; s < 16; ++s) {
+      for (int s = 0; s < V; ++s) {
         const int kx = j + s * Q;
         const float kk = comp == 0 ? __ldg(kt.kvec0 + kx)
                                    : (comp == 1 ? __ldg(kt.kvec0 + outer) : (ok ? __ldg(kt.kvec0 + kz) : 0.f));
         v[s] = make_float2(kk * v[s].y, -kk * v[s].x);
       }
     }
-    run_stages_reg<M, 1, INV, 0, NTW>(v, j, work + c, TK, twr);
+    run_stages_reg<M, 1, INV, 0, NTW, V>(v, j, work + c, TK, twr);
     if constexpr (MODE == MODE_GREEN || MODE == MODE_FUSED || MODE == MODE_POT) {
       const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
       const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
-      for (int s = 0; s < 16; ++s) {
+      for (int s = 0; s < V; ++s) {
         const int kx = j + s * Q;
         const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
         float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
@@ -195,20 +203,20 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
         }
       }
     }
-    if constexpr (MODE == MODE_POT) run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
+    if constexpr (MODE == MODE_POT) run_stages_reg<M, 1, true, 0, NTW, V>(v, j, work + c, TK, twr);
     if constexpr (MODE == MODE_FUSED) {
-      run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
+      run_stages_reg<M, 1, true, 0, NTW, V>(v, j, work + c, TK, twr);
       if (ok) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
+        for (int s = 0; s < V; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
       }
 #pragma unroll
-      for (int s = 0; s < 16; ++s) v[s] = in[(j + s * Q) * TK + c];
-      run_stages_reg<M, 1, true, 0, NTW>(v, j, work + c, TK, twr);
+      for (int s = 0; s < V; ++s) v[s] = in[(j + s * Q) * TK + c];
+      run_stages_reg<M, 1, true, 0, NTW, V>(v, j, work + c, TK, twr);
       if (ok) {
         const float ky0 = __ldg(kt.kvec0 + outer), kz0 = __ldg(kt.kvec0 + kz);
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
+        for (int s = 0; s < V; ++s) {
           const long long idx = base + (long long)(j + s * Q) * stride;
           d1[idx] = make_float2(ky0 * v[s].y, -ky0 * v[s].x);
           d2[idx] = make_float2(kz0 * v[s].y, -kz0 * v[s].x);
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     } else {
       if (ok) {
 #pragma unroll
-        for (int s = 0; s < 16; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
+        for (int s = 0; s < V; ++s) d0[base + (long long)(j + s * Q) * stride] = v[s];
       }
     }
     __syncthreads();  // this tile's buffer is free for the copy issued next iteration
