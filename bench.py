@@ -148,12 +148,10 @@ def source_digest(files=None):
     return h.hexdigest()[:12]
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# (profiles/ncu_fft_y_cfg2.md), keyed by (kernel kind, workload): (bytes, digest, the source
-# files that define the kernel).  Reported only while those files hash to the digest.
-NCU_TRAFFIC = {
-    ("fft_y", "cfg2"): (1.0331e9, "9b1979108d3d", ("fft_engine.cuh", "k_fft_tma.cu")),
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture,
+# keyed by (kernel kind, workload): (bytes, digest, the source files that define the kernel).
+# Reported only while those files hash to the digest.
+NCU_TRAFFIC = {}
 
 
 def dist_setup(args):
