@@ -9,14 +9,15 @@
 // corner) pair is therefore counted by the one CTA that owns the corner cell.
 // Contributions are accumulated in shared memory as fixed-point integers: integer
 // addition is associative, so the result does not depend on thread scheduling, and
-// no float atomics are used.  Mass paints use 2^-24 resolution, each contribution
-// q split as q = hi 2^12 + lo (0 <= lo < 2^12) into two 32-bit accumulators (32-bit
-// shared atomics run ~4x faster than 64-bit ones, and 32-bit conversions avoid the
-// narrow FP64 pipe that 64-bit float <-> integer conversions use); a tile whose
-// particle count could overflow them (count >= 2^17 or count x max mass >= 2^19),
-// masses of 128 or more, and the signed weights of the adjoint use one 64-bit
-// accumulator instead (resolution 2^-24 for masses, so both forms give the same
-// bits; 2^-32 for weights).
+// no float atomics are used.  Mass paints use 2^-24 resolution: each contribution
+// q < 2^31 goes to a 32-bit accumulator with one atomic add, whose returned old value
+// shows when the sum wrapped past 2^32, and then a second word counts the carry
+// (value = carry 2^32 + low word: exact, whatever the order).  A wrap needs a cell of
+// 256 mean cell masses, so nearly every corner costs one 32-bit shared atomic (those
+// run ~4x faster than 64-bit ones, and the 32-bit conversions of the write-out avoid
+// the narrow FP64 pipe that 64-bit float <-> integer conversions use).  Masses of 128
+// or more and the signed weights of the adjoint use one 64-bit accumulator instead
+// (resolution 2^-24 for masses, so both forms give the same bits; 2^-32 for weights).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +33,6 @@ constexpr float kFixW = 4294967296.0f;              // 2^32: signed weights
 constexpr float kUnfixW = 2.3283064365386963e-10f;  // 2^-32
 constexpr float kFixM = 16777216.0f;                // 2^24: masses
 constexpr float kUnfixM = 5.9604644775390625e-08f;  // 2^-24
-constexpr int kLoBits = 12;
 
 // The 14 bucket runs a tile reads, as (neighbour offset o, first class, end class):
 // its own tile (all classes), then for each low-side neighbour o the classes that
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   const uint32_t total = run_pre[14];
   // One particle per thread (coalesced loads in bucket order), its 8 corners added by
   // the same thread.
-  // split: 32-bit accumulators and 32-bit conversions (GB300's FP64 pipe, which runs
-  // the 64-bit float <-> integer conversions, is narrow); w 2^24 < 2^31 needs mmax < 128
-  const bool split = wts == nullptr && mmax < 128.0f && total < (1u << 17) && (float)total * mmax < 524288.0f;
+  // carry form: 32-bit accumulators and conversions (GB300's FP64 pipe, which runs the
+  // 64-bit float <-> integer conversions, is narrow); w 2^24 < 2^31 needs mmax < 128
+  const bool carry = wts == nullptr && mmax < 128.0f;
   const float fix = wts ? kFixW : kFixM;
   const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
   bool bad = false;
@@ -144,10 +144,10 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
       if (inside) {
         const float w = (bx ? fx : 1.0f - fx) * (by ? fy : 1.0f - fy) * (bz ? fz : 1.0f - fz) * m;
         const int ad = cell + bx * kSx + by * kSy + bz;
-        if (split) {
+        if (carry) {
           const unsigned int q = __float2uint_rn(w * fix);  // < 2^31: masses below 128
-          atomicAdd(&acc_hi[ad], q >> kLoBits);
-          atomicAdd(&acc_lo[ad], q & ((1u << kLoBits) - 1u));
+          const unsigned int old = atomicAdd(&acc_lo[ad], q);
+          if (old + q < old) atomicAdd(&acc_hi[ad], 1u);  // the low word wrapped
         } else {
           const long long q = __float2ll_rn(w * fix);
           atomicAdd((unsigned long long*)&acc[ad], (unsigned long long)q);
@@ -165,13 +165,12 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     float fv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (split) {
-        // value = hi 2^12 + lo; for hi, lo < 2^24 both terms are exact floats, so one
-        // correctly rounded addition equals the rounded conversion of the 64-bit sum
+      if (carry) {
+        // value = carry 2^32 + low word: without a carry the correctly rounded 32-bit
+        // conversion is that of the 64-bit sum
         const unsigned int hi = acc_hi[a0 + e], lo = acc_lo[a0 + e];
-        fv[e] = (hi < (1u << 24) && lo < (1u << 24))
-                    ? __fadd_rn(__uint2float_rn(hi) * (float)(1 << kLoBits), __uint2float_rn(lo))
-                    : __ll2float_rn(((long long)hi << kLoBits) + (long long)lo);
+        fv[e] = hi == 0u ? __uint2float_rn(lo)
+                         : __ull2float_rn(((unsigned long long)hi << 32) + (unsigned long long)lo);
       } else {
         fv[e] = __ll2float_rn(acc[a0 + e]);
       }
