@@ -301,14 +301,14 @@ __device__ __forceinline__ uint32_t drift_fixed(uint32_t u, float dscale, float 
   return u + step;
 }
 
-__device__ __forceinline__ void drift_next(const DriftNext& dn, const float (&F)[3], const float* __restrict__ ps,
+__device__ __forceinline__ void drift_next(const DriftNext& dn, const float (&F)[3], const float (&pv)[3],
                                            float K2, int64_t n, uint32_t i, uint32_t ux, uint32_t uy, uint32_t uz,
                                            int shift, int ntl, float* __restrict__ p_out, float* __restrict__ f_out,
                                            uint32_t* __restrict__ u_out) {
   uint32_t uu[3] = {ux, uy, uz};
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float p1 = __fmaf_rn(K2, F[d], ps[(int64_t)d * n + i]);
+    const float p1 = __fmaf_rn(K2, F[d], pv[d]);
     const float p2 = __fmaf_rn(dn.K1, F[d], p1);
     p_out[(int64_t)d * n + i] = p2;
     if (f_out) f_out[(int64_t)d * n + i] = F[d];
@@ -371,13 +371,20 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
     cp_async16(sp + x * kFd4SX + y * kFd4SY + 4 * k, phi + ((size_t)gx * nm + gy) * (size_t)row_pitch + gz);
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
+  // a particle's position, momentum and id are loaded one iteration ahead
+  const bool kick = ps != nullptr && perm == nullptr;
+  auto load = [&](uint32_t j, uint32_t (&uq)[3], float (&pq)[3], uint32_t& idq) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      uq[d] = us[(int64_t)d * n + j];
+      pq[d] = kick ? ps[(int64_t)d * n + j] : 0.0f;
+    }
+    idq = id_out ? ids[j] : 0u;
+  };
   uint32_t i = lo + t;
-  uint32_t ux = 0, uy = 0, uz = 0;
-  if (i < hi) {
-    ux = us[i];
-    uy = us[n + i];
-    uz = us[2 * n + i];
-  }
+  uint32_t cu[3] = {0u, 0u, 0u}, cid = 0u;
+  float cp[3] = {0.f, 0.f, 0.f};
+  if (i < hi) load(i, cu, cp, cid);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const float fscale = 1.0f / (float)(1u << shift);
@@ -385,12 +392,10 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
   bool bad = false;
   for (; i < hi; i += kFd4Threads) {
     const uint32_t inext = i + kFd4Threads;
-    uint32_t nx = 0, ny = 0, nz = 0;
-    if (inext < hi) {
-      nx = us[inext];
-      ny = us[n + inext];
-      nz = us[2 * n + inext];
-    }
+    uint32_t nu[3] = {0u, 0u, 0u}, nid = 0u;
+    float np[3] = {0.f, 0.f, 0.f};
+    if (inext < hi) load(inext, nu, np, nid);
+    const uint32_t ux = cu[0], uy = cu[1], uz = cu[2];
     const int lx = (int)(ux >> shift) - ox, ly = (int)(uy >> shift) - oy, lz = (int)(uz >> shift) - oz;
     if ((unsigned)lx < (unsigned)kTile && (unsigned)ly < (unsigned)kTile && (unsigned)lz < (unsigned)kTile) {
       const float fx = (float)(ux & fmask) * fscale, fy = (float)(uy & fmask) * fscale,
@@ -420,27 +425,30 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
 #pragma unroll
         for (int d = 0; d < 3; ++d) f_out[(int64_t)d * n + j] = F[d];
       } else if constexpr (DRIFT) {
-        drift_next(dn, F, ps, K, n, i, ux, uy, uz, shift, ntl, p_out, f_out, u_out);
-        id_out[i] = ids[i];
+        drift_next(dn, F, cp, K, n, i, ux, uy, uz, shift, ntl, p_out, f_out, u_out);
+        id_out[i] = cid;
       } else {
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          if (p_out) p_out[(int64_t)d * n + i] = __fmaf_rn(K, F[d], ps[(int64_t)d * n + i]);
+          if (p_out) p_out[(int64_t)d * n + i] = __fmaf_rn(K, F[d], cp[d]);
           if (f_out) f_out[(int64_t)d * n + i] = F[d];
         }
         if (u_out) {
           u_out[i] = ux;
           u_out[n + i] = uy;
           u_out[2 * n + i] = uz;
-          id_out[i] = ids[i];
+          id_out[i] = cid;
         }
       }
     } else {
       bad = true;
     }
-    ux = nx;
-    uy = ny;
-    uz = nz;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      cu[d] = nu[d];
+      cp[d] = np[d];
+    }
+    cid = nid;
   }
   if (bad) atomicOr(err, 1);
 }
