@@ -41,8 +41,7 @@ def run_spectra(cfg: RunConfig, n_lin: int, seed: int = 1, nbins: int = 0, k_fs:
     steps = workloads.schedule_paper(5 + n_lin)
     a0 = steps[0][0]
     st = pm.ic(_noise(cfg.nc, seed), a0, k_fs=k_fs)
-    for (a, ah, b) in steps:
-        pm.step(st, a, ah, b)
+    pm.run(st, steps)
     nb = nbins or cfg.nmesh // 2
     out = {}
     k = None
@@ -106,8 +105,7 @@ def sampling_noise(box: float = 256.0, nc: int = 128, nmesh: int = 256, m_total:
             st = pm.ic_pseudo(noise, uni, a0)
         else:
             st = pm.ic(noise, a0)
-        for (a, ah, b) in steps:
-            pm.step(st, a, ah, b)
+        pm.run(st, steps)
         k, P, _ = pm.power(st["u"], st["id"], SPECIES_NU, SPECIES_NU, nbins=nb)
         out.append(P)
         pm.close()

@@ -41,9 +41,11 @@ def run(pm: ParticleMesh, noise, steps, a0: float, k_fs: float = 0.0, checkpoint
     st["f"].copy_(pm.force(st["u"], st["id"]))
     st["f_valid"] = 1
     ckpts = []
+    if not checkpoints:  # chained steps in one pm_run (the same states as stepping)
+        pm.run(st, steps)
+        return st, ckpts
     for (a, ah, b) in steps:
-        if checkpoints:
-            ckpts.append({k: st[k].clone() for k in ("u", "p", "id", "f")} | {"a": a, "f_valid": 1})
+        ckpts.append({k: st[k].clone() for k in ("u", "p", "id", "f")} | {"a": a, "f_valid": 1})
         pm.step(st, a, ah, b)
     return st, ckpts
 
