@@ -148,10 +148,14 @@ def source_digest(files=None):
     return h.hexdigest()[:12]
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture,
-# keyed by (kernel kind, workload): (bytes, digest, the source files that define the kernel).
-# Reported only while those files hash to the digest.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
+# (profiles/ncu_readout_fd4_kick_cfg2.md), keyed by (kernel kind, workload): ((bytes of the
+# launch that carries the next step's kick and drift, bytes of the plain launch), digest,
+# the source files that define the kernel).  Reported only while those files hash to the
+# digest.
+NCU_TRAFFIC = {
+    ("readout_fd4_kick", "cfg2"): ((1685900800.0, 1807801088.0), "01e217c7dd44", ("k_particles.cu", "pm_internal.cuh")),
+}
 
 
 def dist_setup(args):
@@ -377,7 +381,8 @@ def run_ours(args):
         key = (dominant, args.config)
         traffic = None
         if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_digest(NCU_TRAFFIC[key][2]):
-            traffic = NCU_TRAFFIC[key][0]
+            fused, plain = NCU_TRAFFIC[key][0]
+            traffic = (fused * (args.steps - 1) + plain) / args.steps  # per launch, like achieved
         roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"hbm_gbs of {peak_kind}", "algorithmic_bytes_per_launch": alg,
