@@ -92,12 +92,17 @@ def test_shuffled_state_sorts_from_scratch(pm):
     assert ctx.sort_stats()[:2] == (2, 1)
 
 
-@pytest.mark.parametrize("warm", [False, True], ids=["from_ics", "after_a_step"])
-def test_run_equals_repeated_steps_bitwise(pm, warm):
+@pytest.mark.parametrize("warm,learned", [(False, False), (True, False), (False, True)],
+                         ids=["from_ics", "after_a_step", "learned_factor"])
+def test_run_equals_repeated_steps_bitwise(pm, warm, learned):
     """pm_run fuses each step's last readout with the next step's first half kick and
     drift; the state after it must be that of pm_step called once per step, bit for bit."""
     cfg = pm.RunConfig(box=256.0, nmesh=64, nc=32, nsites=8, nshell=10, nfib=3, m_nu=(0.1,) * 3)
     ca, cb = pm.ParticleMesh(cfg), pm.ParticleMesh(cfg)
+    if learned:  # the factor's table is refreshed at every force evaluation in both forms
+        th = inputs.mlp_parameters(6, last_scale=0.5)
+        ca.set_mlp(th)
+        cb.set_mlp(th)
     sa, sb = _state(pm, ca, cfg, seed=4), _state(pm, cb, cfg, seed=4)
     if warm:
         ca.step(sa, 0.05, 0.075, 0.1)
