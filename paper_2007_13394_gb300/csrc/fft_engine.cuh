@@ -97,9 +97,20 @@ __device__ __forceinline__ void dft(float2 (&x)[R]) {
   dft_layers<R, INV, 2>(x);
 }
 
+// Barrier between the shared-memory phases of a stage: the block, or only the warp when
+// every line the warp touches is held by that warp alone (WARP).
+template <bool WARP>
+__device__ __forceinline__ void line_sync() {
+  if constexpr (WARP) {
+    __syncwarp();
+  } else {
+    __syncthreads();
+  }
+}
+
 // One Stockham stage on a line of M points (sub-transform length NS, radix R), V values
 // a thread (value s of thread j is element j + s M / V).
-template <int M, int TWN, int NS, int R, bool INV, bool LAST, int V = 16>
+template <int M, int TWN, int NS, int R, bool INV, bool LAST, int V = 16, bool WARP = false>
 __device__ __forceinline__ void stage(float2 (&v)[V], int j, float2* sm, int cs,
                                       const float2* __restrict__ tw) {
   constexpr int B = V / R;  // butterflies per thread
@@ -129,21 +140,21 @@ __device__ __forceinline__ void stage(float2 (&v)[V], int j, float2* sm, int cs,
     }
   }
   if constexpr (!LAST) {
-    __syncthreads();
+    line_sync<WARP>();
 #pragma unroll
     for (int s = 0; s < V; ++s) v[s] = sm[padi(j + s * Q) * cs];
-    __syncthreads();
+    line_sync<WARP>();
   }
 }
 
-template <int M, int TWN, int NS, bool INV, int V = 16>
+template <int M, int TWN, int NS, bool INV, int V = 16, bool WARP = false>
 __device__ __forceinline__ void run_stages(float2 (&v)[V], int j, float2* sm, int cs,
                                            const float2* __restrict__ tw) {
   constexpr int REM = M / NS;
   constexpr int R = REM >= V ? V : REM;
   constexpr bool LAST = (NS * R == M);
-  stage<M, TWN, NS, R, INV, LAST, V>(v, j, sm, cs, tw);
-  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV, V>(v, j, sm, cs, tw);
+  stage<M, TWN, NS, R, INV, LAST, V, WARP>(v, j, sm, cs, tw);
+  if constexpr (!LAST) run_stages<M, TWN, NS * R, INV, V, WARP>(v, j, sm, cs, tw);
 }
 
 // Twiddles a thread's stages use, held in registers.  They depend only on the thread's

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_r2c(float2* __restrict_
                                                           int pc, const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
   constexpr int LS = M + M / 16 + 2;  // line stride in shared memory
+  constexpr bool WARP = TPL <= 32;    // a row's threads within one warp: warp barriers suffice
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
@@ -53,10 +54,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_r2c(float2* __restrict_
 #pragma unroll
   for (int s = 0; s < 16; ++s) v[s] = ok ? rp[j + s * TPL] : make_float2(0.f, 0.f);
   float2* ls = sm + line * LS;
-  run_stages<M, N, 1, false>(v, j, ls, 1, tw);
+  run_stages<M, N, 1, false, 16, WARP>(v, j, ls, 1, tw);
 #pragma unroll
   for (int s = 0; s < 16; ++s) ls[padi(j + s * TPL)] = v[s];
-  __syncthreads();
+  line_sync<WARP>();
   if (!ok) return;
   for (int k = j; k <= M; k += TPL) {
     float2 zk = ls[padi(k & (M - 1))];
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
                                                           int pc, const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
   constexpr int LS = M + M / 16 + 2;
+  constexpr bool WARP = TPL <= 32;  // a row's threads within one warp: warp barriers suffice
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
     ls[padi(k)] = ok ? rp[k] : make_float2(0.f, 0.f);
   }
   if (j == 0) ls[padi(M)] = ok ? rp[M] : make_float2(0.f, 0.f);
-  __syncthreads();
+  line_sync<WARP>();
   float2 v[16];
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
@@ -100,8 +102,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
     float2 wd = cmul(w, d);
     v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
   }
-  __syncthreads();
-  run_stages<M, N, 1, true>(v, j, ls, 1, tw);
+  line_sync<WARP>();
+  run_stages<M, N, 1, true, 16, WARP>(v, j, ls, 1, tw);
   if (!ok) return;
 #pragma unroll
   for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
