@@ -2,9 +2,9 @@
 
 Test infrastructure only (see the package docstring).
 
-The paper has no adjoint; the benchmark spec asks for gradients of a final-field loss with
-respect to the initial linear modes, for reconstruction.  This module writes the
-chain rule of the forward oracle out step by step:
+The paper has no adjoint; the reconstruction workload needs gradients of a final-field
+loss with respect to the initial linear modes.  This module writes the chain rule of
+the forward oracle out step by step:
 
 * CIC paint rho(c) = sum_i m_i W(x_i - c) with W = prod_d w(x_d - c_d), w the
   1D tent; readout R[M](x) = sum_c W(x - c) M(c).  Their position derivatives use
