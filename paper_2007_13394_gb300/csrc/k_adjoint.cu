@@ -8,6 +8,8 @@
 //   kernel so G_j^T = -G_j):
 //     dL/dx_i = sum_j lambda_F,ij grad R[G_j rho](x_i) + m_i grad R[B](x_i),
 //     B_k = sum_j i D(k_j) g(k) FFT(paint(lambda_F,j))_k, D the gradient kernel.
+//   With the 4-point kernel (and no learned factor) both terms run on one potential
+//   mesh at a time: G_j rho = -S_j phi, and B = G * (sum_j S_j paint(lambda_F,j)).
 // * KDK step VJP (p_h = p0 + K1 F(x0), x1 = x0 + Delta p_h, p1 = p_h + K2 F(x1)).
 // * Zel'dovich IC transpose: s_j = T_j omega with T_j = IFFT diag(S_j) FFT, so
 //   dL/domega = IFFT(sum_j conj(S_j) FFT(lambda_s,j)), neutrino sites with the
@@ -112,6 +114,122 @@ __global__ void k_adj_combine(const float2* __restrict__ a, float2* __restrict__
     } else {
       b[idx] = r;
     }
+  }
+}
+
+// ---- one-mesh force VJP (4-point kernel): the forward force is F_j = -S_j phi with S_j
+// the 4-point stencil along axis j (transfer function i D(k_j)), so
+//   term 1: sum_j lambda_j grad R[F_j] from the potential staged per tile, and
+//   term 2: B = G * (sum_j S_j paint(lambda_j)) (IFFT[g sum_j i D(k_j) FFT(paint_j)]).
+constexpr int kVjpThreads = 256;
+constexpr int kVjpSpanXY = kTile + 5;  // cells -2 .. 18 along x and y
+constexpr int kVjpSpanZ = kTile + 8;   // cells -4 .. 19 along z (16-byte aligned rows)
+constexpr int kVjpChunksZ = kVjpSpanZ / 4;
+constexpr int kVjpStage = kVjpSpanXY * kVjpSpanXY * kVjpChunksZ;
+constexpr int kVjpSY = kVjpSpanZ, kVjpSX = kVjpSpanXY * kVjpSpanZ;
+
+__device__ __forceinline__ void vjp_cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+
+// out[d][perm[i]] = sum_j lambda_j(i) d/dx_d R[F_j](x_i), F_j = -S_j phi, one CTA per
+// tile: the tile's potential with the stencil halo staged like the forward readout's,
+// F_j at the particle's 8 CIC corners from the 56 values, then the CIC weight
+// derivatives (the pattern of k_readout_grad).
+__global__ void __launch_bounds__(kVjpThreads) k_readout_grad_fd4(
+    const uint32_t* __restrict__ us, int64_t n, const uint32_t* __restrict__ bstart,
+    const float* __restrict__ phi, int nm, int shift, int ntl, int row_pitch, float inv12h, float inv_h,
+    const float* __restrict__ lam, const uint32_t* __restrict__ perm, float* __restrict__ out,
+    int* __restrict__ err) {
+  __shared__ __align__(16) float sp[kVjpSpanXY * kVjpSpanXY * kVjpSpanZ];
+  const int t = threadIdx.x;
+  const uint32_t tile = blockIdx.x;
+  const uint32_t lo = bstart[8 * tile], hi = bstart[8 * tile + 8];
+  if (lo == hi) return;
+  const int nt = 1 << ntl;
+  const int ox = (int)(tile >> (2 * ntl)) * kTile, oy = (int)((tile >> ntl) & (nt - 1)) * kTile,
+            oz = (int)(tile & (nt - 1)) * kTile;
+  const int wrap = nm - 1;
+  for (int c = t; c < kVjpStage; c += kVjpThreads) {
+    const int x = c / (kVjpSpanXY * kVjpChunksZ), r = c - x * (kVjpSpanXY * kVjpChunksZ);
+    const int y = r / kVjpChunksZ, k = r - y * kVjpChunksZ;
+    const int gx = (ox + x - 2) & wrap, gy = (oy + y - 2) & wrap, gz = (oz - 4 + 4 * k) & wrap;
+    vjp_cp_async16(sp + x * kVjpSX + y * kVjpSY + 4 * k, phi + ((size_t)gx * nm + gy) * (size_t)row_pitch + gz);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const float fscale = 1.0f / (float)(1u << shift);
+  const uint32_t fmask = (1u << shift) - 1u;
+  bool bad = false;
+  for (uint32_t i = lo + t; i < hi; i += kVjpThreads) {
+    const uint32_t ux = us[i], uy = us[n + i], uz = us[2 * n + i];
+    const int lx = (int)(ux >> shift) - ox, ly = (int)(uy >> shift) - oy, lz = (int)(uz >> shift) - oz;
+    if ((unsigned)lx >= (unsigned)kTile || (unsigned)ly >= (unsigned)kTile || (unsigned)lz >= (unsigned)kTile) {
+      bad = true;
+      continue;
+    }
+    const float fx = (float)(ux & fmask) * fscale, fy = (float)(uy & fmask) * fscale,
+                fz = (float)(uz & fmask) * fscale;
+    const float gx = 1.0f - fx, gy = 1.0f - fy, gz = 1.0f - fz;
+    const float* q = sp + (lx + 2) * kVjpSX + (ly + 2) * kVjpSY + (lz + 4);
+    // F_j at corner (a, b, c) of the cell, Fj[a][b][c] = -S_j phi / ... (scaled below)
+    float Fx[2][2][2], Fy[2][2][2], Fz[2][2][2];
+    auto line = [](const float* q0, int S, float& c0, float& c1) {  // stencil sums at corners 0, 1
+      const float m2 = q0[-2 * S], m1 = q0[-S], p0 = q0[0], p1 = q0[S], p2 = q0[2 * S], p3 = q0[3 * S];
+      c0 = 8.0f * (p1 - m1) - (p2 - m2);
+      c1 = 8.0f * (p2 - p0) - (p3 - m1);
+    };
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        line(q + a * kVjpSY + b, kVjpSX, Fx[0][a][b], Fx[1][a][b]);  // x line at (y, z) = (a, b)
+        line(q + a * kVjpSX + b, kVjpSY, Fy[a][0][b], Fy[a][1][b]);  // y line at (x, z) = (a, b)
+        line(q + a * kVjpSX + b * kVjpSY, 1, Fz[a][b][0], Fz[a][b][1]);  // z line at (x, y) = (a, b)
+      }
+    }
+    const float l0 = lam[i], l1 = lam[n + i], l2 = lam[2 * n + i];
+    float o[3] = {0.f, 0.f, 0.f};
+    const float (*Fs[3])[2][2] = {Fx, Fy, Fz};
+    const float ls[3] = {l0, l1, l2};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float (*v)[2][2] = Fs[j];
+      const float dX = gy * (gz * (v[1][0][0] - v[0][0][0]) + fz * (v[1][0][1] - v[0][0][1])) +
+                       fy * (gz * (v[1][1][0] - v[0][1][0]) + fz * (v[1][1][1] - v[0][1][1]));
+      const float dY = gx * (gz * (v[0][1][0] - v[0][0][0]) + fz * (v[0][1][1] - v[0][0][1])) +
+                       fx * (gz * (v[1][1][0] - v[1][0][0]) + fz * (v[1][1][1] - v[1][0][1]));
+      const float dZ = gx * (gy * (v[0][0][1] - v[0][0][0]) + fy * (v[0][1][1] - v[0][1][0])) +
+                       fx * (gy * (v[1][0][1] - v[1][0][0]) + fy * (v[1][1][1] - v[1][1][0]));
+      o[0] += ls[j] * dX;
+      o[1] += ls[j] * dY;
+      o[2] += ls[j] * dZ;
+    }
+    const int64_t dst = perm ? (int64_t)perm[i] : (int64_t)i;
+    const float scale = -inv12h * inv_h;  // F_j = -(stencil sum) / (12 H); d/dx: 1 / H
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[(int64_t)d * n + dst] = scale * o[d];
+  }
+  if (bad) atomicOr(err, 1);
+}
+
+// B (+)= S_j A on real meshes (row pitch rp): the 4-point stencil along axis j, periodic.
+__global__ void k_stencil_axis(const float* __restrict__ A, float* __restrict__ B, int nm, int rp, int axis,
+                               float inv12h, int accumulate) {
+  const int x = blockIdx.x / nm, y = blockIdx.x % nm;
+  const int w = nm - 1;
+  const size_t row = ((size_t)x * nm + y) * rp;
+  for (int z = threadIdx.x; z < nm; z += blockDim.x) {
+    auto at = [&](int o) -> float {  // A at offset o along the axis
+      if (axis == 0) return __ldg(A + ((size_t)((x + o) & w) * nm + y) * rp + z);
+      if (axis == 1) return __ldg(A + ((size_t)x * nm + ((y + o) & w)) * rp + z);
+      return __ldg(A + row + ((z + o) & w));
+    };
+    const float v = inv12h * (8.0f * (at(1) - at(-1)) - (at(2) - at(-2)));
+    B[row + z] = accumulate ? B[row + z] + v : v;
   }
 }
 
@@ -277,6 +395,28 @@ int force_vjp(pm_ctx* c, const uint32_t* u, const uint32_t* id, int64_t n, const
   float* realA = reinterpret_cast<float*>(c->meshA);
   float* realB = reinterpret_cast<float*>(c->meshB);
   const int rp = 2 * c->g.pc;
+  if (!learned && (c->cfg.flags & (PM_FLAG_SPECTRAL_KERNEL | PM_FLAG_KSPACE_GRADIENT)) == 0) {
+    // one mesh at a time, five FFT passes a term (see k_readout_grad_fd4)
+    const float inv12h = (float)((double)c->g.n / (12.0 * c->cfg.box));
+    const float inv_h = (float)(c->g.n / c->cfg.box);
+    paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s);
+    fft_potential(c, c->g, c->meshA, s);
+    {
+      LaunchScope L(c, s, K_ADJOINT);
+      k_readout_grad_fd4<<<(unsigned)(c->nt * c->nt * c->nt), kVjpThreads, 0, s>>>(
+          c->us, n, c->bstart, realA, c->g.n, 32 - c->g.logn, c->ntl, rp, inv12h, inv_h, lam_s, c->vals[0], grad,
+          c->err_dev);
+    }
+    for (int j = 0; j < 3; ++j) {
+      paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s, lam_s + (int64_t)j * n);
+      LaunchScope L(c, s, K_ADJOINT);
+      k_stencil_axis<<<(unsigned)(c->g.n * c->g.n), 256, 0, s>>>(realA, realB, c->g.n, rp, j, inv12h, j > 0);
+    }
+    fft_potential(c, c->g, c->meshB, s);
+    const float* m[1] = {realB};
+    readout_grad(c, n, m, 1, rp, nullptr, c->vals[0], grad, true, s);
+    return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+  }
   // term 1: sum_j lambda_j grad R[G_j rho]
   paint_tiles(c, c->us, c->ids, n, PM_SPECIES_ALL, realA, rp, s);
   if (learned) {
