@@ -22,7 +22,11 @@
  *   potential   phi_k = -(3/2) Omega_m0 delta_k / N^3 / k^2, phi_0 = 0;
  *   force       F_j = IFFT[-i D(k_j) phi_k] with the 4-point finite-difference
  *               gradient D(k) = (8 sin kH - sin 2kH) / (6H) (0 on the Nyquist
- *               index), read out with the paint's CIC weights.  No window
+ *               index), read out with the paint's CIC weights.  Computed by
+ *               default as minus the 4-point stencil [8 (phi(x+H) - phi(x-H)) -
+ *               (phi(x+2H) - phi(x-2H))] / (12 H) of the real potential at the CIC
+ *               corners (its transfer function is i D(k)), so one inverse
+ *               transform serves all three components.  No window
  *               deconvolution: with the mesh finer than the CDM lattice (the
  *               paper's mesh is twice the CDM grid) a deconvolved spectral
  *               kernel amplifies the lattice's alias modes and breaks linear
@@ -43,8 +47,8 @@
  *
  * Memory and ownership: every particle and output array passed in is owned
  * by the caller; a context owns its scratch (three padded complex meshes of
- * N * N * (N/2 + 2) float2 each -- two with flags bit 0 or nmesh 2048 -- plus sort buffers for
- * n_max particles).
+ * N * N * (N/2 + 2) float2 each -- two with flags bit 0 or nmesh 2048; the default
+ * force path uses one -- plus sort buffers for n_max particles).
  * Arrays are structure-of-arrays: u[3 * n] holds the x plane, then y, then z.
  * "Device" pointers are CUDA device memory of the context's device; "host"
  * pointers are ordinary (preferably pinned) host memory.
