@@ -204,7 +204,9 @@ int pm_step(pm_ctx* ctx, pm_state* st, double a0, double ah, double a1, void* st
  * KDK with the two half kicks of a step boundary in one pass over the particles), so
  * there is no separate kick/drift pass between steps and f is written by the last step
  * only.  On return: as pm_step after the last step.  Stream ordered, with one host
- * synchronisation per step (the sort's choice of method). */
+ * synchronisation per step (the sort's choice of method).  On an error status the
+ * state is undefined (steps before the failing one have already applied the next
+ * step's kick and drift). */
 int pm_run(pm_ctx* ctx, pm_state* st, const double* schedule, int64_t nsteps, void* stream);
 
 /* pm_step on HOST arrays (u[3n], p[3n], id[n], f[3n]): copies in, steps, copies out;
