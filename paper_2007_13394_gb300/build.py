@@ -6,6 +6,7 @@ link step produces ``paper_2007_13394_gb300/libpmnu.so``.  Objects go to
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -41,22 +42,32 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(verbose_ptxas: bool = False, force: bool = False) -> str:
-    """Compile every source and link libpmnu.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def _up_to_date() -> bool:
     newest = max(os.path.getmtime(os.path.join(CSRC, f)) for f in os.listdir(CSRC))
     newest = max(newest, os.path.getmtime(os.path.join(HERE, "..", "include", "pm.h")))
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) > newest and not verbose_ptxas:
+    return os.path.exists(LIB) and os.path.getmtime(LIB) > newest
+
+
+def build(verbose_ptxas: bool = False, force: bool = False) -> str:
+    """Compile every source and link libpmnu.so; returns the library path.  Processes
+    that build at the same time (the ranks of one job) take turns on a lock file, and
+    each re-checks the library once it holds the lock."""
+    os.makedirs(BUILD, exist_ok=True)
+    if not force and not verbose_ptxas and _up_to_date():
         return LIB
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    with open(os.path.join(BUILD, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not verbose_ptxas and _up_to_date():
+            return LIB
+        extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
+        tmp = LIB + ".tmp"
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
     return LIB
 
 
