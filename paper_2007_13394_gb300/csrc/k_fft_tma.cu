@@ -79,8 +79,9 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 // padded work layout (rounded up to 128 bytes, the alignment of a tensor copy's
 // destination) because the Stockham stages run in the buffer of the tile just read.
 // Two-transform passes (potential, fused) keep two tile buffers and a separate work
-// area: their longer register life makes the extra barrier and the 80-register cap of
-// the in-buffer layout cost more than the deeper prefetch gains (measured).
+// area: measured with 16 values a thread, where the in-buffer layout meant three CTAs
+// at 80 registers, the spills and the extra barrier cost more than the deeper prefetch
+// gained; the potential pass is close to issue-bound, so prefetch depth is not its limit.
 // values a thread holds: 8 (radix-8 stages, 64 registers, twice the resident warps of
 // the 16-value form) from 256-point lines up
 template <int LOGM>
