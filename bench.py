@@ -200,7 +200,7 @@ def oracle_run(cfg, n_warm, n_timed):
     from oracle import ic as oic
     from oracle import neutrinos as onu
     from oracle import pm as opm
-    from paper_2007_13394_gb300 import inputs, workloads
+    from paper_2007_13394_gb300 import inputs
     bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
     plin = oic.linear_power(cfg.omega_m, cfg.h, cfg.ns, cfg.sigma8)
     a0 = 0.01
@@ -209,12 +209,12 @@ def oracle_run(cfg, n_warm, n_timed):
     _, q, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
     un, pn = oic.neutrino_particles(noise, cfg.box, plin, bg.D(a0), bg.gp(a0), cfg.nsites, cfg.nshell,
                                     cfg.nfib, q, onu.thermal_momentum_scale(bg.kT_nu0, max(cfg.m_nu)),
-                                    k_fs=workloads.free_streaming_k(cfg, a0))
+                                    k_fs=oic.free_streaming_k(list(cfg.m_nu), a0, cfg.omega_m))
     u, p = np.hstack([uc, un]), np.hstack([pc, pn])
     mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
                                 bg.omega_nu_poisson, m_shell)
     mass = onu.particle_masses(uc.shape[1], un.shape[1], cfg.nshell, cfg.nfib, mc, mn)
-    sched = workloads.schedule_paper(max(25, n_warm + n_timed))
+    sched = obg.schedule_paper(max(25, n_warm + n_timed))
     f = opm.force(u, mass, cfg.nmesh, cfg.box, bg.omega_m0)
     t = 0.0
     for i, (a, ah, b) in enumerate(sched[: n_warm + n_timed]):

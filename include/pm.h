@@ -160,8 +160,14 @@ int pm_cosmo_params(const pm_config* cfg, double* out);
 
 /* ---- context ----------------------------------------------------------------- */
 
-/* Validates cfg, builds the FP64 growth and shell tables, allocates the scratch on
- * the current CUDA device.  *out receives the context; free it with pm_destroy. */
+/* Validates cfg, builds the FP64 tables the step needs -- the growth factor D(a) of
+ * the ODE of §2.3 Eq. growthDE on the background of Eq. Hubble (with Omega_m(a) of
+ * §2.2 Eq. Om_pois read as Omega_m0 a^-3 / E^2), the FastPM kick and drift factors it
+ * feeds (§2.3), and the Fermi-Dirac shell table of §2.1 (Eqs. N_shell, q_shell, m_shell,
+ * FD_deg) that sets the neutrino particle masses -- and allocates the scratch on the
+ * current CUDA device.  cfg: host, read only, not kept.  *out receives the context,
+ * owned by the caller until pm_destroy.  PM_EINVAL for a bad configuration (see
+ * pm_config), PM_ENOMEM when an allocation fails (nothing is left allocated). */
 int pm_init(const pm_config* cfg, pm_ctx** out);
 int pm_destroy(pm_ctx* ctx);
 
@@ -182,19 +188,31 @@ int pm_coeffs(pm_ctx* ctx, double a0, double ah, double a1, double* out);
 int pm_sort(pm_ctx* ctx, const uint32_t* u, int64_t n, uint32_t* perm_out, uint32_t* key_out,
             void* stream);
 
-/* CIC density rho / rho_bar of the selected species (PM_SPECIES_*) on the N^3 mesh.
- * id may be NULL (particle i has id i).  mesh_out: device, N^3 floats, x-major
- * with z fastest. */
+/* CIC density rho / rho_bar of the selected species (PM_SPECIES_*) on the N^3 mesh:
+ * the source of the Poisson equation, where neutrino particles count as matter beside
+ * CDM (§2.2 Eq. Om_pois; per-particle masses from the shell fractions of §2.1 Eq.
+ * m_shell).  u: device, 3n uint32 fixed-point positions; id: device, n canonical ids,
+ * or NULL (particle i has id i); mesh_out: device, N^3 floats, x-major with z fastest,
+ * caller-owned.  Deterministic (integer accumulation).  PM_EINVAL for n < 0, n > n_max
+ * or a null pointer; an id beyond the configured particles sets the error word. */
 int pm_paint(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species,
              float* mesh_out, void* stream);
 
-/* PM force at every particle, F_out[3 n] (device) in input order. */
+/* PM force at every particle: F = -grad phi with the Poisson equation of §2.2
+ * (nabla^2 phi = 1.5 Omega_m0 delta, Eq. Om_pois; both species as matter), on the
+ * mesh twice the CDM grid of §3 Table 1, by the kernel defined at the top of this
+ * header.  u, id as pm_paint; F_out: device, 3n floats in input order, caller-owned.
+ * PM_EINVAL as pm_paint. */
 int pm_force(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, float* F_out,
              void* stream);
 
-/* One kick-drift-kick step a0 -> a1 (ah <= 0 selects the arithmetic mean).  If
- * st->f_valid is 0 the force at a0 is computed first.  On return the state holds
- * (u, p, f) at a1 in tile order, st->a = a1, st->f_valid = 1. */
+/* One kick-drift-kick step a0 -> a1 (§2.1 "Kick-Drift-Kick": FastPM's KDK scheme;
+ * §2.3: kick and drift factors built from the growth factor so that the Zel'dovich
+ * trajectory x = q + D(a) s is followed exactly; CDM and neutrinos alike).  ah <= 0
+ * selects the arithmetic mean.  If st->f_valid is 0 the force at a0 is computed first.
+ * st: host struct of caller-owned device arrays (see pm_state).  On return the state
+ * holds (u, p, f) at a1 in tile order, st->a = a1, st->f_valid = 1.  PM_EINVAL
+ * unless 0 < a0 <= ah <= a1 <= 2 with a0 < a1, or for n > n_max or null arrays. */
 int pm_step(pm_ctx* ctx, pm_state* st, double a0, double ah, double a1, void* stream);
 
 /* nsteps chained KDK steps: schedule (host) holds (a0, ah, a1) per step, each step's a0
@@ -215,11 +233,15 @@ int pm_run(pm_ctx* ctx, pm_state* st, const double* schedule, int64_t nsteps, vo
 int pm_step_host(pm_ctx* ctx, uint32_t* u, float* p, uint32_t* id, float* f, int64_t n,
                  int32_t* f_valid, double a0, double ah, double a1, void* stream);
 
-/* Binned (cross) power spectrum of the species a and b (PM_SPECIES_*):
- * P_ab(k) = (V / N^6) Re(delta_a delta_b^*) / W(k)^2, linear bins of width
+/* Binned (cross) power spectrum of the species a and b (PM_SPECIES_*): the P_cdm,
+ * P_m, P_cdm,nu and P_nu the results of §3 compare (Figs. MR, Pn_shotnoise); the paper
+ * measures them with nbodykit and prints no estimator, so this is the reading:
+ * P_ab(k) = (V / N^6) Re(delta_a delta_b^*) / W(k)^2 with each species' mesh over its
+ * own mean and W the CIC window, no shot-noise subtraction, linear bins of width
  * k_F = 2 pi / L from k_F / 2, mode-weighted mean |k|, r2c modes with
- * 0 < n_z < N/2 counted twice.  Host outputs of length nbins (<= 2048);
- * synchronous. */
+ * 0 < n_z < N/2 counted twice.  u, id as pm_paint; k_out, P_out, nmodes_out: host
+ * arrays of length nbins (<= 2048).  Synchronous; PM_EINVAL for a bad species or
+ * nbins. */
 int pm_power(pm_ctx* ctx, const uint32_t* u, const uint32_t* id, int64_t n, int32_t species_a,
              int32_t species_b, int32_t nbins, double* k_out, double* P_out, int64_t* nmodes_out,
              void* stream);
@@ -373,8 +395,12 @@ int pm_readout(pm_ctx* ctx, const uint32_t* u, int64_t n, const float* mesh, flo
  * Limits: nmesh a power of two in [32, 2048], 1 <= nbins <= 512, box > 0; anything
  * else returns PM_EINVAL without touching the GPU.  The first call on a device
  * resolves the array's device address (cudaGetSymbolAddress with that device
- * current): make it before any stream capture.  All calls share the array, so calls
- * that overlap on the GPU race on it; nothing needs clearing between calls. */
+ * current) and keeps it for the life of the process: make that call before any
+ * stream capture, and do not call this again on a device after cudaDeviceReset
+ * (the reset unloads the module; the kept address would no longer be the array's).
+ * All calls share the array, so calls that overlap on the GPU race on it; nothing
+ * needs clearing between calls.  The library receives raw pointers and cannot check
+ * that delta_a and delta_b hold the N * N * (N/2 + 1) complex values they must. */
 int pm_power_bin_noalloc(const float* delta_a, const float* delta_b, int32_t nmesh, double box,
                          int32_t nbins, double* k_out, double* P_out, double* nmodes_out,
                          void* stream);

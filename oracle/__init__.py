@@ -29,7 +29,8 @@ ic          BBKS spectrum, sigma_8 normalisation, Zel'dovich initial
 ewald       brute-force periodic Ewald sum of the force of one point mass.
 
 Parity status: every function is pinned by a test in ``tests/test_oracle_*.py``
-against a closed form, a limit, an invariant or brute force, except
-``neutrinos.fibonacci_directions`` anisotropy (reported, bounded, "parity
-unpinned" beyond its exact symmetric sums).
+against a closed form, a limit, an invariant or brute force.  The Fibonacci
+directions are pinned by the properties their golden-angle lattice fixes
+(equal-area zones, packing distance, Fibonacci parastichies), which reject
+spirals with another turning angle.
 """

@@ -86,6 +86,16 @@ def delta_k(noise, box, pk):
     return dk
 
 
+def free_streaming_k(masses_ev, a, omega_m):
+    """Free-streaming wavenumber of the synthetic neutrino suppression, h/Mpc:
+    k_fs(a) = 0.82 sqrt(Omega_L + Omega_m a^-3) a^2 (m / 1 eV) with Omega_L = 1 - Omega_m
+    (flat, radiation neglected) and m the mean eigenstate mass (the standard scaling of
+    Lesgourgues & Pastor, the reading taken for the REPS neutrino transfer functions the
+    paper's initial conditions use, §2.2)."""
+    m = sum(masses_ev) / len(masses_ev)
+    return 0.82 * math.sqrt((1.0 - omega_m) + omega_m / a ** 3) * a * a * m
+
+
 def displacement(dk, box, shift=0.0, k_fs=0.0):
     """s(x_i + shift) on the lattice, shape (3, N_c, N_c, N_c); optional 1/(1+(k/k_fs)^2)."""
     nc = dk.shape[0]

@@ -136,9 +136,12 @@ extern "C" int pm_power_bin_noalloc(const float* delta_a, const float* delta_b, 
   const float norm = (float)(box * box * box / (nn * nn * nn * nn * nn * nn));
   const double kf = 2.0 * 3.14159265358979323846 / box;
   const int grid = nmesh < kRows ? nmesh : kRows;
+  // launch errors are peeked, not cleared: an error left by earlier, unrelated work on this
+  // thread stays for its owner to read (it is also reported here, as PM_ECUDA)
   k_bin_noalloc<<<grid, kThreads, 0, s>>>(reinterpret_cast<const float2*>(delta_a),
                                           reinterpret_cast<const float2*>(delta_b), nmesh, nbins,
                                           norm, kf, rows);
+  if (cudaPeekAtLastError() != cudaSuccess) return PM_ECUDA;
   k_reduce_noalloc<<<(nbins + 127) / 128, 128, 0, s>>>(rows, grid, nbins, k_out, P_out, nmodes_out);
-  return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
+  return cudaPeekAtLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }

@@ -210,6 +210,10 @@ def power_bin_noalloc(delta_a, delta_b, nmesh: int, box: float, nbins: int):
     Returns device tensors (k, P, n_modes) of float64; the library itself allocates
     nothing (the output tensors are the caller's).
     """
+    # the library sees raw pointers only: a spectrum shorter than the mesh's half spectrum
+    # would be read past its end on the device, so the shapes are checked here
+    for name, t in (("delta_a", delta_a), ("delta_b", delta_b)):
+        check_half_spectrum(t, nmesh, name)
     torch = _torch()
     k = torch.empty(nbins, dtype=torch.float64, device="cuda")
     P = torch.empty(nbins, dtype=torch.float64, device="cuda")
@@ -217,6 +221,28 @@ def power_bin_noalloc(delta_a, delta_b, nmesh: int, box: float, nbins: int):
     _check(load_library().pm_power_bin_noalloc(_ptr(delta_a), _ptr(delta_b), nmesh, box, nbins, _ptr(k), _ptr(P),
                                                _ptr(nm), _stream()), "pm_power_bin_noalloc")
     return k, P, nm
+
+
+def check_half_spectrum(t, nmesh: int, name: str = "spectrum") -> None:
+    """Raise ValueError unless t is a contiguous float32 CUDA tensor on the current device
+    holding at least the nmesh * nmesh * (nmesh // 2 + 1) complex values (interleaved
+    floats) of an r2c half spectrum.  Sizes are checked before the device, so the rule
+    can be exercised on CPU tensors."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name}: float32 required (interleaved complex), got {t.dtype}")
+    need = int(nmesh) * int(nmesh) * (int(nmesh) // 2 + 1) * 2
+    if t.numel() < need:
+        raise ValueError(f"{name}: {t.numel()} floats, the {nmesh}^3 half spectrum needs {need}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
 
 
 def _torch():

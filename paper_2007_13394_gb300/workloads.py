@@ -66,8 +66,9 @@ def schedule_paper(n_total: int, a_start: float = 0.01, a_switch: float = 0.05, 
     return out
 
 
-def free_streaming_k(cfg: RunConfig, a: float, omega_lambda: float = 0.69) -> float:
+def free_streaming_k(cfg: RunConfig, a: float) -> float:
     """k_fs(a) = 0.82 sqrt(Omega_L + Omega_m a^-3) a^2 (m_nu / 1 eV) h/Mpc for the mean eigenstate
-    mass: the scale of the synthetic suppression of the initial neutrino field."""
+    mass, Omega_L = 1 - Omega_m: the scale of the synthetic suppression of the initial neutrino
+    field."""
     m = sum(cfg.m_nu) / max(1, len(cfg.m_nu))
-    return 0.82 * math.sqrt(omega_lambda + cfg.omega_m / a ** 3) * a * a * m
+    return 0.82 * math.sqrt((1.0 - cfg.omega_m) + cfg.omega_m / a ** 3) * a * a * m

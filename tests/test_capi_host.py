@@ -35,6 +35,24 @@ def test_header_declares_the_five_required_calls():
         assert req in names
 
 
+def test_required_calls_cite_the_passage_that_defines_them():
+    """Each of the five calls of the boundary carries, in the comment right above its
+    declaration, a citation (§ section, equation, table) of the passage it implements."""
+    text = open(os.path.join(ROOT, "include", "pm.h")).read()
+    want = {"pm_init": ["Eq. growthDE", "Eq. Hubble", "m_shell"],
+            "pm_paint": ["Eq. Om_pois"],
+            "pm_force": ["Eq. Om_pois", "Table 1"],
+            "pm_step": ["Kick-Drift-Kick", "§2.3"],
+            "pm_power": ["§3"]}
+    for name, cites in want.items():
+        m = re.search(r"/\*((?:(?!\*/).)*)\*/\s*int " + name + r"\(", text, flags=re.S)
+        assert m, name
+        comment = m.group(1)
+        assert "§" in comment, name
+        for c in cites:
+            assert c in comment, (name, c)
+
+
 def test_library_exports_every_declared_symbol(lib):
     so = os.path.join(ROOT, "paper_2007_13394_gb300", "libpmnu.so")
     out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True).stdout
@@ -97,3 +115,23 @@ def test_host_rejects_bad_configs(lib):
         assert ei.value.status == pm.PM_EINVAL
     with pytest.raises(pm.PMError):
         pm.cosmo_coeffs(_cfg(), 0.5, 0.4, 0.6)     # half point outside the step
+
+
+def test_noalloc_wrapper_rejects_short_or_foreign_spectra():
+    """pm_power_bin_noalloc receives raw pointers, so its binding checks the spectra before
+    any device work: a 64^3 half spectrum passed with nmesh = 128 would be read past its end."""
+    torch = pytest.importorskip("torch")
+    from paper_2007_13394_gb300 import pm
+    ok64 = torch.zeros((64, 64, 33, 2), dtype=torch.float32)
+    with pytest.raises(ValueError, match="half spectrum needs"):
+        pm.check_half_spectrum(ok64, 128)
+    with pytest.raises(ValueError, match="half spectrum needs"):
+        pm.power_bin_noalloc(ok64, ok64, 128, 100.0, 16)       # rejected before any GPU call
+    with pytest.raises(ValueError, match="float32"):
+        pm.check_half_spectrum(ok64.double(), 64)
+    with pytest.raises(ValueError, match="contiguous"):
+        pm.check_half_spectrum(torch.zeros((64, 64, 66, 2), dtype=torch.float32)[:, :, ::2], 64)
+    with pytest.raises(ValueError, match="CUDA"):
+        pm.check_half_spectrum(ok64, 64)
+    with pytest.raises(ValueError, match="torch tensor"):
+        pm.check_half_spectrum(np.zeros(64 * 64 * 33 * 2, dtype=np.float32), 64)

@@ -108,9 +108,9 @@ def test_cfg2_physics_power_spectra_match_oracle_at_128(pm):
     several minutes.)"""
     from paper_2007_13394_gb300 import workloads
     cfg = workloads.cfg2_parity()
-    sched = workloads.schedule_paper(25)
+    sched = obg.schedule_paper(25)
     a0 = sched[0][0]
-    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, a0, 1, workloads.free_streaming_k(cfg, a0))
+    bg, noise, u, p, mass, ncdm = oracle_ics(cfg, a0, 1, oic.free_streaming_k(list(cfg.m_nu), a0, cfg.omega_m))
     f = opm.force(u, mass, cfg.nmesh, cfg.box, bg.omega_m0)
     uo, po = u.copy(), p.copy()
     for (a, ah, b) in sched:
@@ -135,10 +135,19 @@ def test_cfg2_physics_power_spectra_match_oracle_at_128(pm):
         k, P, nm = ctx.power(st["u"], st["id"], species_a=sa, species_b=sb, nbins=nb)
         ko, Po, no = ref[(sa, sb)]
         sel = (no > 0) & (ko < kny / 2)
-        # the cross-spectrum crosses zero: measure it against its Cauchy-Schwarz bound
-        scale = np.abs(Po) if sa == sb else np.sqrt(ref[(1, 1)][1] * ref[(2, 2)][1])
-        rel = np.abs(P[sel] - Po[sel]) / scale[sel]
-        print(f"\nP_{sa}{sb}: max |P - P_oracle| / scale for k < k_Ny/2 = {rel.max():.2e}")
+        # per bin within 0.1 %; the cross-spectrum also crosses zero, so it is held per bin
+        # wherever it is at least a tenth of its Cauchy-Schwarz bound sqrt(P_cc P_nunu), and
+        # against that bound everywhere
+        rel = np.abs(P[sel] - Po[sel]) / np.abs(Po[sel])
+        if sa != sb:
+            cs = np.sqrt(ref[(1, 1)][1] * ref[(2, 2)][1])[sel]
+            big = np.abs(Po[sel]) >= 0.1 * cs
+            assert big.sum() >= sel.sum() // 2, "the cross-spectrum is small in most bins"
+            rel_cs = np.abs(P[sel] - Po[sel]) / cs
+            print(f"\nP_12: max |P - P_oracle| / sqrt(P_11 P_22) for k < k_Ny/2 = {rel_cs.max():.2e}")
+            assert rel_cs.max() < 1e-3
+            rel = rel[big]
+        print(f"\nP_{sa}{sb}: max |P - P_oracle| / |P_oracle| per bin, k < k_Ny/2 = {rel.max():.2e}")
         assert rel.max() < 1e-3, f"P_{sa}{sb}"
     ctx.sync()
 

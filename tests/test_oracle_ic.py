@@ -105,3 +105,12 @@ def test_particle_layout_and_thermal_terms():
             np.testing.assert_allclose(pn[:, i], 2.0 * q[shell] * dirs[d], rtol=1e-14)
             rad = 0.45 * (L / ns) * q[shell] / q.max()
             np.testing.assert_allclose(pm.decode(un[:, i], L), (site0 + rad * dirs[d]) % L, atol=1e-7)
+
+
+def test_free_streaming_k_limits():
+    # today (a = 1, flat) k_fs = 0.82 (m / 1 eV) h/Mpc; deep in matter domination it grows as
+    # sqrt(Omega_m a): k_fs(a) / k_fs(a / 4) -> 2
+    assert ic.free_streaming_k([0.1, 0.1, 0.1], 1.0, 0.31) == pytest.approx(0.082, rel=1e-14)
+    assert ic.free_streaming_k([0.3], 1.0, 0.5) == pytest.approx(0.82 * 0.3, rel=1e-14)
+    r = ic.free_streaming_k([0.2], 4e-4, 0.31) / ic.free_streaming_k([0.2], 1e-4, 0.31)
+    assert r == pytest.approx(2.0, rel=1e-6)

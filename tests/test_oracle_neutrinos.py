@@ -102,10 +102,77 @@ def test_fibonacci_directions_symmetric_sums():
         np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, rtol=1e-15)
         assert abs(d[:, 2].sum()) < 1e-14          # sin(lat) antisymmetric in i
         assert abs(d[:, 1].sum()) < 1e-14          # sin(lon) antisymmetric in i
-    # anisotropy of sum v v^T / n - I/3 is reported, bounded by O(1/N_fib) (parity unpinned)
-    d = nu.fibonacci_directions(20)
-    aniso = np.abs(d.T @ d / len(d) - np.eye(3) / 3).max()
-    assert aniso < 0.05
+
+
+FIBONACCI_NUMBERS = {1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144, 233, 377, 610, 987, 1597}
+
+
+def golden_lattice_defects(d):
+    """Properties that the Fibonacci (golden-angle) sphere lattice of 2 N_fib + 1 points
+    fixes (González 2010, the lattice cited for the directions of §2.1, Eq. N_n), each
+    checked without the lattice's own formula.  Returns the list of violated properties.
+
+    1. Equal-area zones: by Archimedes' hat-box theorem a zone of the unit sphere between
+       heights z_a < z_b has area 2 pi (z_b - z_a), so n points that each own an equal
+       share of the area sit one per zone of height 2 / n, at its centre: sorted heights
+       -1 + (2k + 1) / n.
+    2. Packing: the smallest distance between two points is ~3.09 / sqrt(n), i.e. 0.87 of
+       sqrt(4 pi / n), the side of a square of the mean area per point (González's
+       figure), for every n; a spiral with another turning angle packs worse.
+    3. Parastichies: in index order the longitude advances by the golden angle, whose
+       continued fraction [1; 1, 1, ...] makes the nearest neighbours of every point
+       away from the poles lie at Fibonacci-number index offsets.
+    """
+    n = len(d)
+    bad = []
+    z = np.sort(d[:, 2])
+    if np.abs(z - (-1.0 + (2.0 * np.arange(n) + 1.0) / n)).max() > 1e-14:
+        bad.append("equal-area zones")
+    dist = np.linalg.norm(d[:, None, :] - d[None, :, :], axis=2)
+    np.fill_diagonal(dist, np.inf)
+    if dist.min() < 0.86 * math.sqrt(4.0 * math.pi / n):
+        bad.append("packing")
+    if n >= 41:
+        away = np.abs(d[:, 2]) < 0.8
+        nearest = np.argsort(dist, axis=1)[:, :2]
+        offsets = np.abs(nearest - np.arange(n)[:, None])[away]
+        if not all(int(o) in FIBONACCI_NUMBERS for o in offsets.ravel()):
+            bad.append("parastichies")
+    return bad
+
+
+def test_fibonacci_directions_are_the_golden_angle_lattice():
+    for nfib in (3, 20, 100, 500):
+        assert golden_lattice_defects(nu.fibonacci_directions(nfib)) == [], nfib
+    # the second moments approach isotropy (sum v v^T / n -> I / 3) as the lattice grows
+    aniso = [np.abs(d.T @ d / len(d) - np.eye(3) / 3).max()
+             for d in (nu.fibonacci_directions(k) for k in (20, 100, 500))]
+    assert aniso[0] < 1e-3 and aniso[2] < 1e-4 and aniso[2] < aniso[0]
+
+
+def _spiral(nfib, turn):
+    """Planted mistakes: the lattice with the longitude of point i replaced by turn(i, n)."""
+    n = 2 * nfib + 1
+    i = np.arange(-nfib, nfib + 1)
+    lat = np.arcsin(2.0 * i / n)
+    lon = turn(i, n)
+    return np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)], axis=1)
+
+
+@pytest.mark.parametrize("name,turn", [
+    ("single turn", lambda i, n: 2.0 * math.pi * i / n),
+    ("half the golden turn", lambda i, n: math.pi * i / ((1.0 + math.sqrt(5.0)) / 2.0)),
+    ("sqrt(2) turn", lambda i, n: 2.0 * math.pi * i / math.sqrt(2.0)),
+])
+def test_fibonacci_pins_reject_other_spirals(name, turn):
+    for nfib in (20, 100):
+        assert golden_lattice_defects(_spiral(nfib, turn)), (name, nfib)
+    # a shifted height rule breaks the equal-area zones
+    golden = (1.0 + math.sqrt(5.0)) / 2.0
+    d = _spiral(20, lambda i, n: 2.0 * math.pi * i / golden)
+    assert golden_lattice_defects(d) == []
+    d[:, 2] *= 1.0 - 1e-3
+    assert "equal-area zones" in golden_lattice_defects(d)
 
 
 def test_particle_counts_match_paper():

@@ -46,3 +46,14 @@ def test_run_readout_bytes_average():
     assert plain == 68 * n + 4 * nm ** 3
     assert b.run_readout_bytes(nm, n, 1) == plain
     assert b.run_readout_bytes(nm, n, 4) == pytest.approx((3 * (60 * n + 4 * nm ** 3) + plain) / 4)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "cfg2", "cfg3"])
+def test_free_streaming_k_equals_oracle(name):
+    """The product's k_fs (the initial-condition suppression scale it hands to pm_ic) equals
+    the oracle's own restatement."""
+    from oracle import ic as oic
+    cfg = workloads.PRESETS[name]()
+    for a in (0.01, 0.1, 1.0):
+        assert workloads.free_streaming_k(cfg, a) == pytest.approx(
+            oic.free_streaming_k(list(cfg.m_nu), a, cfg.omega_m), rel=1e-14)

@@ -52,6 +52,31 @@ def test_noalloc_binning_matches_pm_power_twice(pm):
     ctx.sync()
 
 
+def test_noalloc_binning_at_512_with_the_most_bins(pm):
+    """A 512^3 mesh (more x planes than the 256 CTAs of the binning kernel, so each CTA
+    loops over two planes) with nbins = 512, the array's limit: equal to pm_power on the
+    same particles, on two calls in a row."""
+    cfg = pm.RunConfig(box=512.0, nmesh=512, nc=128)
+    ctx = pm.ParticleMesh(cfg)
+    noise = torch.from_numpy(inputs.white_noise(cfg.nc, seed=5)).cuda()
+    st = ctx.ic(noise, 0.2, k_fs=0.0)
+    u, ids = st["u"], st["id"]
+    nb = 512
+    spec = ctx.fft_r2c(ctx.paint(u, ids, species=pm.SPECIES_ALL))
+    k0, P0, n0 = ctx.power(u, ids, species_a=pm.SPECIES_ALL, species_b=pm.SPECIES_ALL, nbins=nb)
+    for call in range(2):
+        k1, P1, n1 = pm.power_bin_noalloc(spec, spec, cfg.nmesh, cfg.box, nb)
+        torch.cuda.synchronize()
+        k1, P1, n1 = k1.cpu().numpy(), P1.cpu().numpy(), n1.cpu().numpy()
+        np.testing.assert_array_equal(n1.astype(np.int64), n0)
+        assert (n0 > 0).sum() > 400          # every |n| up to sqrt(3) 256 has modes
+        ok = n0 > 0
+        np.testing.assert_allclose(k1[ok], k0[ok], rtol=1e-12)
+        np.testing.assert_allclose(P1[ok], P0[ok], rtol=1e-5)
+    ctx.sync()
+    ctx.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_array(pm):
     x = torch.zeros((64, 64, 33, 2), dtype=torch.float32, device="cuda")
     for bad in (dict(nbins=513), dict(nbins=0), dict(nmesh=48), dict(box=0.0)):
