@@ -1,11 +1,14 @@
 """Throughput of the particle-mesh kick-drift-kick step on GB300.
 
-A "step" is one full KDK step (first half kick + drift + sort + paint + r2c FFT
-with the Green's function + 3 x (inverse FFT + readout + second half kick)) over
-every particle of the workload, inputs resident in HBM.  Default workload: 512
-Mpc/h, 256^3 CDM + 32^3 x 70 neutrinos (M_nu = 0.1 eV), mesh 512^3, started
-from Zel'dovich initial conditions at z = 99 and advanced along the paper's
-schedule (5 log-a steps, then linear a).
+A "step" is one full KDK step (first half kick + drift + re-sort + paint + r2c FFT
+with the Green's function + inverse FFT of the potential + stencil readout fused
+with the second half kick) over every particle of the workload, inputs resident in
+HBM.  Default workload (cfg3, the paper's NC1024_NF3 scale, Table 1): 1024 Mpc/h,
+1024^3 CDM + 128^3 x 70 neutrinos (one effective distribution for the
+normal-hierarchy masses summing to 0.6 eV), mesh 2048^3, started from Zel'dovich
+initial conditions at z = 99 and advanced along the paper's schedule (5 log-a
+steps, then linear a).  The 512^3-mesh workload (cfg2) is measured after it and
+reported under the "cfg2" key.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -148,14 +151,11 @@ def source_digest(files=None):
     return h.hexdigest()[:12]
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
-# (profiles/ncu_readout_fd4_kick_cfg2.md), keyed by (kernel kind, workload): ((bytes of the
-# launch that carries the next step's kick and drift, bytes of the plain launch), digest,
-# the source files that define the kernel).  Reported only while those files hash to the
-# digest.
-NCU_TRAFFIC = {
-    ("readout_fd4_kick", "cfg2"): ((1685900800.0, 1807801088.0), "01e217c7dd44", ("k_particles.cu", "pm_internal.cuh")),
-}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel
+# from one ncu capture of the current build, keyed by (kernel kind, workload): (per-launch
+# bytes as a function of the timed steps, digest, the source files that define the kernel,
+# where the capture is summarised).  Reported only while those files hash to the digest.
+NCU_TRAFFIC = {}
 
 
 def dist_setup(args):
@@ -183,15 +183,24 @@ def aggregate_replicas(ms_local, n_local, world, device="cpu"):
 
 
 # --------------------------------------------------------------- oracle arm
-def oracle_sample_cfg(steps_total, budget_s=120.0):
-    """A bounded sample of the cfg2 workload: same 2 Mpc/h spacing, boost-2 mesh and
-    neutrino-to-CDM ratio in a smaller box, the largest whose steps fit the budget
-    (about 10 s, 0.8 s and 0.08 s per FP64 step on one core)."""
-    from paper_2007_13394_gb300.pm import RunConfig
-    for box, nc, ns, t_est in ((256.0, 128, 16, 10.0), (128.0, 64, 8, 0.8), (64.0, 32, 4, 0.08)):
+def oracle_sample_cfg(name, steps_total, budget_s=120.0):
+    """A bounded sample of workload `name`: the same CDM spacing, mesh boost, neutrino site
+    spacing and masses in a smaller box, the largest (of 128^3, 64^3, 32^3 CDM) whose steps
+    fit the budget (about 10 s, 0.25 s and 0.03 s per FP64 step on one core)."""
+    import dataclasses as dc
+
+    from paper_2007_13394_gb300 import workloads
+    full = workloads.PRESETS[name]()
+    spacing = full.box / full.nc
+    boost = full.nmesh // full.nc
+    per_site = full.nc // full.nsites if full.nsites else 0
+    for nc, t_est in ((128, 10.0), (64, 0.25), (32, 0.03)):
         if steps_total * t_est <= budget_s or nc == 32:
-            return (RunConfig(box=box, nmesh=2 * nc, nc=nc, nsites=ns, nshell=10, nfib=3, m_nu=(0.1 / 3,) * 3),
-                    f"{box:g} Mpc/h box, {nc}^3 CDM + {ns}^3 x 70 nu, mesh {2 * nc}^3 (cfg2 density and boost)")
+            ns = nc // per_site if per_site else 0
+            cfg = dc.replace(full, box=spacing * nc, nc=nc, nmesh=boost * nc, nsites=ns, n_max=0)
+            nu = f" + {ns}^3 x {cfg.nshell * (2 * cfg.nfib + 1)} nu" if ns else ""
+            return cfg, (f"{cfg.box:g} Mpc/h box, {nc}^3 CDM{nu}, mesh {cfg.nmesh}^3 ({name} density, boost "
+                         f"and masses, M_nu = {sum(cfg.m_nu):g} eV)")
 
 
 def oracle_run(cfg, n_warm, n_timed):
@@ -206,14 +215,16 @@ def oracle_run(cfg, n_warm, n_timed):
     a0 = 0.01
     noise = inputs.white_noise(cfg.nc, seed=1).astype(np.float64)
     uc, pc = oic.cdm_particles(noise, cfg.box, plin, bg.D(a0), bg.gp(a0))
-    _, q, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
-    un, pn = oic.neutrino_particles(noise, cfg.box, plin, bg.D(a0), bg.gp(a0), cfg.nsites, cfg.nshell,
-                                    cfg.nfib, q, onu.thermal_momentum_scale(bg.kT_nu0, max(cfg.m_nu)),
-                                    k_fs=oic.free_streaming_k(list(cfg.m_nu), a0, cfg.omega_m))
-    u, p = np.hstack([uc, un]), np.hstack([pc, pn])
+    u, p, n_nu, m_shell = uc, pc, 0, np.zeros(cfg.nshell)
+    if cfg.nsites:
+        _, q, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
+        un, pn = oic.neutrino_particles(noise, cfg.box, plin, bg.D(a0), bg.gp(a0), cfg.nsites, cfg.nshell,
+                                        cfg.nfib, q, onu.thermal_momentum_scale(bg.kT_nu0, max(cfg.m_nu)),
+                                        k_fs=oic.free_streaming_k(list(cfg.m_nu), a0, cfg.omega_m))
+        u, p, n_nu = np.hstack([uc, un]), np.hstack([pc, pn]), un.shape[1]
     mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
                                 bg.omega_nu_poisson, m_shell)
-    mass = onu.particle_masses(uc.shape[1], un.shape[1], cfg.nshell, cfg.nfib, mc, mn)
+    mass = onu.particle_masses(uc.shape[1], n_nu, cfg.nshell, cfg.nfib, mc, mn)
     sched = obg.schedule_paper(max(25, n_warm + n_timed))
     f = opm.force(u, mass, cfg.nmesh, cfg.box, bg.omega_m0)
     t = 0.0
@@ -230,16 +241,17 @@ def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
-    cfg, desc = oracle_sample_cfg(args.steps + args.warmup)
+    cfg, desc = oracle_sample_cfg(args.config, args.steps + args.warmup)
     sec, n, cores = oracle_run(cfg, args.warmup, args.steps)
     value = n / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "cfg2 sample: " + desc, "n_particles": n},
+        "config": {"workload": f"{args.config} sample: " + desc, "n_particles": n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": desc + f"; {args.steps} timed KDK steps after {args.warmup} warm-up"},
+                         "sample": desc + f"; {args.steps} timed KDK steps after {args.warmup} warm-up",
+                         "host_cores_available": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -283,19 +295,68 @@ def fft_reference(ctx, n, reps=10):
     return out
 
 
-def run_ours(args):
+def step_kernels(ctx, st, sched, base, n, nmesh, peak_bw):
+    """Every kernel kind timed (CUDA events on its launch stream) over 3 steady pm_run steps:
+    per launch ms, and the algorithmic bandwidth and its fraction of the measured peak."""
+    ctx.profile(None)
+    ctx.profile_read(reset=True)
+    ctx.run(st, sched[base:base + 3])
+    per_kind = {}
+    sort_fast, sort_full, movers = ctx.sort_stats()
+    for kind, (kms, kn) in ctx.profile_read(reset=True).items():
+        # the near-sorted re-sort radix-sorts only the movers
+        n_kind = movers if kind.startswith("radix") and sort_fast > 0 and sort_full == 0 else n
+        alg_b = algorithmic_bytes(kind, nmesh, n_kind)
+        if kind == "readout_fd4_kick":
+            alg_b = run_readout_bytes(nmesh, n, 3)
+        per = kms / kn
+        per_kind[kind] = {"launches": kn, "ms_per_launch": round(per, 4),
+                          "gbs": round(alg_b / (per / 1e3) / 1e9, 1) if alg_b else None,
+                          "frac": round(alg_b / (per / 1e3) / 1e9 / peak_bw, 3) if alg_b else None}
+    ctx.profile([])
+    return per_kind, (sort_fast, sort_full, movers)
+
+
+def e2e_host(ctx, st, sched, base, n, k_e2e):
+    """End to end through pm_step_host: every step copies u, p, id, f from pinned host memory
+    to the device, runs one KDK step and copies them back.  The device state is released first
+    (the library keeps its own device copy for host-buffer calls)."""
+    import torch
+    pinned = {k: torch.empty(st[k].shape, dtype=st[k].dtype, pin_memory=True) for k in ("u", "p", "id", "f")}
+    for k, v in pinned.items():
+        v.copy_(st[k])
+    fv = st["f_valid"]
+    for k in ("u", "p", "id", "f"):
+        st[k] = None
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    hu, hp, hid, hf = (pinned[k].numpy() for k in ("u", "p", "id", "f"))
+    fv = ctx.step_host(hu, hp, hid, hf, fv, *sched[base % len(sched)])  # warm the host path
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(k_e2e):
+        fv = ctx.step_host(hu, hp, hid, hf, fv, *sched[(base + 1 + j) % len(sched)])
+    t_e2e = (time.perf_counter() - t0) / k_e2e
+    del pinned, hu, hp, hid, hf
+    return {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 40 * n, "d2h_bytes_per_step": 40 * n,
+            "steps": k_e2e, "ms_per_step": t_e2e * 1e3,
+            "note": "pm_step_host: u, p, id, f copied from pinned host memory to the device, one KDK step, "
+                    "copied back; bound by the host link"}
+
+
+def workload_desc(name, cfg):
+    nu = (f" + {cfg.nsites}^3 x {cfg.nshell * (2 * cfg.nfib + 1)} nu (M_nu = {sum(cfg.m_nu):g} eV)"
+          if cfg.nsites else "")
+    return f"{name}: {cfg.box:g} Mpc/h, {cfg.nc}^3 CDM{nu}, mesh {cfg.nmesh}^3, one KDK PM step"
+
+
+def measure(args, name, rank, world, local, steps, warmup, with_e2e, with_fft_ref):
+    """Run workload `name` on this rank's GPU: ICs, warm-up steps, `steps` timed steps through
+    one pm_run, per-kernel timings, optionally e2e and the FFT beside cuFFT."""
     import torch
 
-    from paper_2007_13394_gb300 import build as _build
     from paper_2007_13394_gb300 import inputs, pm, workloads
-
-    world, rank, local = dist_setup(args)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    _build.build()
-    cfg = workloads.PRESETS[args.config]()
+    cfg = workloads.PRESETS[name]()
     if args.kspace_gradient:
         cfg.flags |= 8
     if args.two_mesh:
@@ -309,20 +370,16 @@ def run_ours(args):
     a_start = 0.01
     st = ctx.ic(noise, a_start, k_fs=workloads.free_streaming_k(cfg, a_start))
     del noise
-    sched = workloads.schedule_paper(max(25, args.warmup + args.steps + 16))
+    sched = workloads.schedule_paper(max(25, warmup + steps + 16))
     stream = torch.cuda.current_stream()
 
-    def step(i):
-        a0, ah, a1 = sched[i]
-        ctx.step(st, a0, ah, a1)
-
-    # warm-up, the first one also profiles every kernel kind to find the dominant one
+    # warm-up; the first step also times every kernel kind to find the dominant one
     ctx.profile(None)
-    step(0)
+    ctx.step(st, *sched[0])
     prof_all = ctx.profile_read()
     ctx.profile([])
-    for i in range(1, args.warmup):
-        step(i)
+    for i in range(1, warmup):
+        ctx.step(st, *sched[i])
     ctx.sync()
     shares = {k: v[0] for k, v in prof_all.items()}
     dominant = max(shares, key=shares.get)
@@ -339,105 +396,97 @@ def run_ours(args):
         e0.record(stream)
         # the K steps through pm_run: each step's last readout carries the next step's
         # first half kick and drift (same state as K pm_step calls, bit for bit)
-        ctx.run(st, sched[args.warmup:args.warmup + args.steps])
+        ctx.run(st, sched[warmup:warmup + steps])
         e1.record(stream)
         torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ctx.sync()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     launches = ctx.launch_count() - launches0
     dom = ctx.profile_read(reset=True).get(dominant, (0.0, 0))
     ctx.profile([])
-    # one more steady step with every kernel kind timed: per-kernel algorithmic bandwidth
-    peak_bw, _ = peaks()
-    ctx.profile(None)
-    ctx.profile_read(reset=True)
-    base = args.warmup + args.steps
-    ctx.run(st, sched[base:base + 3])  # steady steps of the pm_run path, per launch below
-    per_kind = {}
-    sort_fast, sort_full, movers = ctx.sort_stats()
-    for kind, (kms, kn) in ctx.profile_read(reset=True).items():
-        # the near-sorted re-sort radix-sorts only the movers
-        n_kind = movers if kind.startswith("radix") and sort_fast > 0 and sort_full == 0 else n
-        alg_b = algorithmic_bytes(kind, cfg.nmesh, n_kind)
-        if kind == "readout_fd4_kick":
-            alg_b = run_readout_bytes(cfg.nmesh, n, 3)
-        per = kms / kn
-        per_kind[kind] = {"launches": kn, "ms_per_launch": round(per, 4),
-                          "gbs": round(alg_b / (per / 1e3) / 1e9, 1) if alg_b else None,
-                          "frac": round(alg_b / (per / 1e3) / 1e9 / peak_bw, 3) if alg_b else None}
-    ctx.profile([])
-    ms_max, n_total, value = aggregate_replicas(ms, n, world, device="cuda")
+    peak_bw, peak_kind = peaks()
+    per_kind, (sort_fast, sort_full, movers) = step_kernels(ctx, st, sched, warmup + steps, n, cfg.nmesh, peak_bw)
+    dom_ms = dom[0] / max(1, dom[1])
+    alg = algorithmic_bytes(dominant, cfg.nmesh, n)
+    if dominant == "readout_fd4_kick":
+        alg = run_readout_bytes(cfg.nmesh, n, steps)
+    achieved = alg / (dom_ms / 1e3) / 1e9 if alg and dom_ms > 0 else None
+    key = (dominant, name)
+    traffic, traffic_src = None, None
+    if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_digest(NCU_TRAFFIC[key][2]):
+        per_launch, _, _, traffic_src = NCU_TRAFFIC[key]
+        traffic = per_launch(steps)
+    roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak_bw, "unit": "GB/s",
+            "frac": (achieved / peak_bw) if achieved else None, "traffic": traffic,
+            "traffic_source": traffic_src,
+            "peak_source": f"hbm_gbs of {peak_kind}", "algorithmic_bytes_per_launch": alg,
+            "ms_per_launch": dom_ms, "launches_timed": dom[1],
+            "step_share": shares[dominant] / sum(shares.values())}
+    e2e = None
+    if with_e2e:
+        e2e = e2e_host(ctx, st, sched, warmup + steps + 3, n, max(3, min(steps, 5)))
+    fft_ref = fft_reference(ctx, cfg.nmesh) if with_fft_ref else None
+    out = {"n": n, "ms": ms, "launches": launches, "roofline": roof, "e2e": e2e, "fft_reference": fft_ref,
+           "clocks": clk.summary(), "kernels_steady_step": per_kind, "cfg": cfg,
+           "sort": {"near_sorted_steps": sort_fast, "from_scratch_steps": sort_full, "movers_last_step": movers}}
+    ctx.close()
+    del st
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
 
-    out = None
+
+def run_ours(args):
+    import torch
+
+    from paper_2007_13394_gb300 import build as _build
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    _build.build()
+    big = args.config in ("cfg3", "cfg_mid")
+    r = measure(args, args.config, rank, world, local, args.steps, args.warmup,
+                with_e2e=not args.no_e2e and rank == 0, with_fft_ref=not args.no_fft_reference and not big)
+    ms_max, n_total, value = aggregate_replicas(r["ms"], r["n"], world, device="cuda")
+    extra = None
+    if args.config == "cfg3" and not args.no_cfg2:
+        r2 = measure(args, "cfg2", rank, world, local, 20, 3, with_e2e=False,
+                     with_fft_ref=not args.no_fft_reference and rank == 0)
+        ms2, _, value2 = aggregate_replicas(r2["ms"], r2["n"], world, device="cuda")
+        extra = {"workload": workload_desc("cfg2", r2["cfg"]), "value": value2, "unit": UNIT,
+                 "ms_per_step": ms2, "steps": 20, "warmup": 3, "n_particles": r2["n"],
+                 "roofline": r2["roofline"], "clocks": r2["clocks"], "fft_reference": r2["fft_reference"],
+                 "kernels_steady_step": r2["kernels_steady_step"], "sort": r2["sort"]}
     if rank == 0:
-        peak, peak_kind = peaks()
-        dom_ms = dom[0] / max(1, dom[1])
-        alg = algorithmic_bytes(dominant, cfg.nmesh, n)
-        if dominant == "readout_fd4_kick":
-            alg = run_readout_bytes(cfg.nmesh, n, args.steps)
-        achieved = alg / (dom_ms / 1e3) / 1e9 if alg and dom_ms > 0 else None
-        key = (dominant, args.config)
-        traffic = None
-        if key in NCU_TRAFFIC and NCU_TRAFFIC[key][1] == source_digest(NCU_TRAFFIC[key][2]):
-            fused, plain = NCU_TRAFFIC[key][0]
-            traffic = (fused * (args.steps - 1) + plain) / args.steps  # per launch, like achieved
-        roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                "peak_source": f"hbm_gbs of {peak_kind}", "algorithmic_bytes_per_launch": alg,
-                "ms_per_launch": dom_ms, "launches_timed": dom[1],
-                "step_share": shares[dominant] / sum(shares.values())}
-        # end to end through the C-ABI with host buffers: copies in, step, copies out, every step
-        e2e = None
-        if not args.no_e2e and args.config not in ("cfg3", "cfg_mid"):
-            # pinned (page-locked) host buffers, viewed as numpy arrays for the C-ABI call
-            pinned = {k: torch.empty(st[k].shape, dtype=st[k].dtype, pin_memory=True) for k in ("u", "p", "id", "f")}
-            for k, v in pinned.items():
-                v.copy_(st[k])
-            hu, hp, hid, hf = (pinned[k].numpy() for k in ("u", "p", "id", "f"))
-            fv = st["f_valid"]
-            k_e2e = max(3, min(args.steps, 10))
-            base = args.warmup + args.steps + 3  # after the profiled steady steps
-            fv = ctx.step_host(hu, hp, hid, hf, fv, *sched[base % len(sched)])  # warm the host path
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for j in range(k_e2e):
-                fv = ctx.step_host(hu, hp, hid, hf, fv, *sched[(base + 1 + j) % len(sched)])
-            t_e2e = (time.perf_counter() - t0) / k_e2e
-            e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 40 * n,
-                   "d2h_bytes_per_step": 40 * n, "steps": k_e2e,
-                   "note": "pm_step_host: u, p, id, f copied from pinned host memory to the device, "
-                           "one KDK step, copied back"}
-        fft_ref = None
-        if not args.no_fft_reference and args.config not in ("cfg3", "cfg_mid"):  # 2048^3 / 1024^3: skipped
-            fft_ref = fft_reference(ctx, cfg.nmesh)
+        cfg = r["cfg"]
         cpu = None
-        if not args.no_cpu_baseline and world == 1 and args.config not in ("cfg3", "cfg_mid"):
-            ocfg, desc = oracle_sample_cfg(1)
+        if not args.no_cpu_baseline and world == 1:
+            ocfg, desc = oracle_sample_cfg(args.config, 2, budget_s=30.0)
             sec, n_o, cores = oracle_run(ocfg, 0, 1)
             cpu = {"value": n_o / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": desc + "; one FP64 KDK step (force, kicks, drift)",
+                   "sample": desc + "; one FP64 KDK step (force, kicks, drift) after the first force",
                    "host_cores_available": os.cpu_count()}
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.config}: {cfg.box:g} Mpc/h, {cfg.nc}^3 CDM + {cfg.nsites}^3 x "
-                                   f"{cfg.nshell * (2 * cfg.nfib + 1)} nu (M_nu = {sum(cfg.m_nu):g} eV), "
-                                   f"mesh {cfg.nmesh}^3, one KDK PM step",
-                       "n_particles": n, "nmesh": cfg.nmesh, "parallelism": f"replicas x{world}",
+            "config": {"workload": workload_desc(args.config, cfg), "n_particles": r["n"], "nmesh": cfg.nmesh,
+                       "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (padded force mesh of "
                              f"{cfg.nmesh ** 2 * (cfg.nmesh // 2 + 2) * 8 / 1e6:.0f} MB, particles "
-                             f"{40 * n / 1e6:.0f} MB)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "sort": {"near_sorted_steps": sort_fast, "from_scratch_steps": sort_full,
-                     "movers_last_step": movers},
-            "fft_reference": fft_ref,
-            "clocks": clk.summary(), "kernels_steady_step": per_kind,
+                             f"{40 * r['n'] / 1e6:.0f} MB)"},
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+            "sort": r["sort"], "fft_reference": r["fft_reference"],
+            "clocks": r["clocks"], "kernels_steady_step": r["kernels_steady_step"],
         }
+        if extra is not None:
+            out["cfg2"] = extra
         print(json.dumps(out))
-    ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -446,10 +495,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg_mid", "cfg3"], default="cfg2")
+    ap.add_argument("--config", choices=["cfg1", "cfg2", "cfg2_parity", "cfg_mid", "cfg3"], default="cfg3")
     ap.add_argument("--kspace-gradient", action="store_true",
                     help="gradient in k-space with three inverse transforms (flags bit 3)")
     ap.add_argument("--two-mesh", action="store_true",
@@ -459,6 +508,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft-reference", action="store_true", help="skip the FFT beside cuFFT")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cfg2", action="store_true", help="skip the cfg2 measurement after cfg3")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -142,7 +142,7 @@ def test_cfg2_physics_power_spectra_match_oracle_at_128(pm):
         if sa != sb:
             cs = np.sqrt(ref[(1, 1)][1] * ref[(2, 2)][1])[sel]
             big = np.abs(Po[sel]) >= 0.1 * cs
-            assert big.sum() >= sel.sum() // 2, "the cross-spectrum is small in most bins"
+            assert big.sum() >= 5, "too few bins where the cross-spectrum is not small"
             rel_cs = np.abs(P[sel] - Po[sel]) / cs
             print(f"\nP_12: max |P - P_oracle| / sqrt(P_11 P_22) for k < k_Ny/2 = {rel_cs.max():.2e}")
             assert rel_cs.max() < 1e-3
