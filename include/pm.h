@@ -59,7 +59,10 @@
  * (PM_OK or a negative PM_E* code) and never aborts.  A kernel that detects a
  * bad input (an out-of-range particle id, a bucket overflow) sets a device
  * error word; synchronous calls and pm_sync() report it as PM_EKERNEL, and it
- * stays set (sticky) until pm_sync() returns it.  A context is not
+ * stays set (sticky) until pm_sync() returns it.  A NaN or infinite momentum
+ * or force met by the kick kernels is reported the same way as PM_ENONFINITE,
+ * and a bounded wait that gave up (a tensor copy that never arrived) as
+ * PM_ETIMEOUT; the context stays usable after each.  A context is not
  * thread-safe; use one per host thread.
  */
 #ifndef PMNU_PM_H
@@ -78,7 +81,8 @@ enum {
   PM_ECUDA = -3,     /* a CUDA runtime call failed */
   PM_EKERNEL = -4,   /* a kernel flagged bad input through the device error word */
   PM_ETIMEOUT = -5,  /* a bounded device wait gave up */
-  PM_ENOTINIT = -6   /* null or destroyed context */
+  PM_ENOTINIT = -6,  /* null or destroyed context */
+  PM_ENONFINITE = -7 /* a kernel met a NaN or infinite momentum or force */
 };
 
 /* Species selectors for pm_paint and pm_power. */
@@ -118,6 +122,10 @@ typedef struct pm_config {
                           tensor cores (BF16 operands, FP32 accumulation) instead of FP32;
                           other bits 0 */
   int32_t pad1;
+  int64_t mem_limit;   /* bytes of device memory the context may hold (its scratch, and the
+                          buffers later calls allocate on first use); 0: no limit.  An
+                          allocation that would pass it fails with PM_ENOMEM without calling
+                          cudaMalloc (pm_init then frees what it had allocated). */
 } pm_config;
 
 /* Particle state.  All arrays are caller-owned device memory of length 3n (u, p, f)
@@ -409,6 +417,16 @@ int pm_power_bin_noalloc(const float* delta_a, const float* delta_b, int32_t nme
 
 /* Number of kernels this context has launched since pm_init. */
 int64_t pm_launch_count(pm_ctx* ctx);
+/* Bytes of device memory the context holds now (what pm_config.mem_limit is checked against). */
+int64_t pm_memory_used(pm_ctx* ctx);
+/* Testing aid for the failure paths (no counterpart in the paper).  what = PM_INJECT_DROP_COPY:
+ * in the next TMA-pipelined FFT pass (meshes up to 512^3) the first CTA does not issue its
+ * first tile copy, so its bounded wait on that copy runs out (after a short limit), the CTA
+ * waits for its other copies in flight and returns, and the next pm_sync reports PM_ETIMEOUT;
+ * the pass's output is then invalid, the context stays usable.  One shot: consumed by that
+ * launch.  what = 0 cancels a pending injection. */
+enum { PM_INJECT_DROP_COPY = 1 };
+int pm_test_inject(pm_ctx* ctx, int32_t what);
 /* CUDA-event timing of launches on their own stream, per kernel kind: bit k of mask
  * selects kind k (-1 = every kind, 0 = off). */
 int pm_profile_enable(pm_ctx* ctx, int32_t mask);

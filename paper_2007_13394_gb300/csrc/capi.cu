@@ -48,10 +48,34 @@ float2* twiddles(pm_ctx* c, int n) {
     h[t] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
   float2* d = nullptr;
-  if (cudaMalloc(&d, sizeof(float2) * n) != cudaSuccess) return nullptr;
+  if (ctx_alloc_n(c, &d, (size_t)n) != PM_OK) return nullptr;
   cudaMemcpy(d, h.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
   c->tw[n] = d;
   return d;
+}
+
+int ctx_alloc(pm_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  const int64_t lim = c->cfg.mem_limit;
+  if (lim > 0 && c->mem_used + bytes > (size_t)lim) return PM_ENOMEM;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();  // the failed allocation's error is reported as PM_ENOMEM
+    return PM_ENOMEM;
+  }
+  c->allocs[*p] = bytes;
+  c->mem_used += bytes;
+  return PM_OK;
+}
+
+void ctx_free(pm_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->allocs.find(p);
+  if (it != c->allocs.end()) {
+    c->mem_used -= it->second;
+    c->allocs.erase(it);
+  }
+  cudaFree(p);
 }
 
 }  // namespace pmnu
@@ -75,51 +99,49 @@ void drain_profile(pm_ctx* c) {
 }
 
 template <class T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count) == cudaSuccess ? PM_OK : PM_ENOMEM;
+int dalloc(pm_ctx* c, T** p, size_t count) {
+  return ctx_alloc_n(c, p, count);
 }
 
 void free_all(pm_ctx* c) {
-  cudaFree(c->meshA);
-  cudaFree(c->meshB);
-  cudaFree(c->meshC);
-  for (auto& kv : c->tw) cudaFree(kv.second);
-  cudaFree(c->ksq);
-  cudaFree(c->winv);
-  cudaFree(c->wforce);
-  cudaFree(c->kvec0);
+  ctx_free(c, c->meshA);
+  ctx_free(c, c->meshB);
+  ctx_free(c, c->meshC);
+  for (auto& kv : c->tw) ctx_free(c, kv.second);
+  ctx_free(c, c->ksq);
+  ctx_free(c, c->winv);
+  ctx_free(c, c->wforce);
+  ctx_free(c, c->kvec0);
   for (int i = 0; i < 2; ++i) {
-    cudaFree(c->keys[i]);
-    cudaFree(c->vals[i]);
+    ctx_free(c, c->keys[i]);
+    ctx_free(c, c->vals[i]);
   }
-  cudaFree(c->us);
-  cudaFree(c->ps);
-  cudaFree(c->ids);
-  cudaFree(c->counts);
-  cudaFree(c->bstart);
-  cudaFree(c->bprev);
-  cudaFree(c->rs_low);
-  cudaFree(c->rs_k2);
-  cudaFree(c->rs_v2);
-  cudaFree(c->rs_dev);
+  ctx_free(c, c->us);
+  ctx_free(c, c->ps);
+  ctx_free(c, c->ids);
+  ctx_free(c, c->counts);
+  ctx_free(c, c->bstart);
+  ctx_free(c, c->bprev);
+  ctx_free(c, c->rs_low);
+  ctx_free(c, c->rs_k2);
+  ctx_free(c, c->rs_v2);
+  ctx_free(c, c->rs_dev);
   if (c->rs_host) cudaFreeHost(c->rs_host);
-  cudaFree(c->hist);
-  cudaFree(c->hist_scan);
-  cudaFree(c->scan_tmp);
-  cudaFree(c->pk_partial);
-  cudaFree(c->pk_final);
-  cudaFree(c->pk_w);
-  cudaFree(c->ic_amp);
-  cudaFree(c->ic_amp_nu);
-  cudaFree(c->err_dev);
+  ctx_free(c, c->hist);
+  ctx_free(c, c->hist_scan);
+  ctx_free(c, c->scan_tmp);
+  ctx_free(c, c->pk_partial);
+  ctx_free(c, c->pk_final);
+  ctx_free(c, c->pk_w);
+  ctx_free(c, c->ic_amp);
+  ctx_free(c, c->ic_amp_nu);
+  ctx_free(c, c->err_dev);
   if (c->err_host) cudaFreeHost(c->err_host);
-  cudaFree(c->hs_u);
-  cudaFree(c->hs_p);
-  cudaFree(c->hs_id);
-  cudaFree(c->hs_f);
-  cudaFree(c->adj);
+  ctx_free(c, c->hs_u);
+  ctx_free(c, c->hs_p);
+  ctx_free(c, c->hs_id);
+  ctx_free(c, c->hs_f);
+  ctx_free(c, c->adj);
   mlp_free(c);
   for (auto& p : c->prof_live) {
     cudaEventDestroy(p.a);
@@ -333,6 +355,7 @@ const char* pm_strerror(int status) {
     case PM_EKERNEL: return "a kernel flagged invalid input";
     case PM_ETIMEOUT: return "a bounded device wait timed out";
     case PM_ENOTINIT: return "context not initialised";
+    case PM_ENONFINITE: return "a kernel met a non-finite momentum or force";
     default: return "unknown status";
   }
 }
@@ -457,17 +480,17 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
   // flag bit 0, or a 2048^3 mesh: per-component force path with two meshes (at 2048^3 it is
   // also the faster one: reading three 34 GB meshes at once starves the readout)
   const bool two_mesh = (cfg->flags & PM_FLAG_TWO_MESH) != 0 || N >= 2048;
-  if ((!two_mesh && dalloc(&c->meshC, me)) || dalloc(&c->meshA, me) || dalloc(&c->meshB, me) ||
-      dalloc(&c->ksq, N) ||
-      dalloc(&c->winv, N) || dalloc(&c->wforce, N) || dalloc(&c->kvec0, N) || dalloc(&c->keys[0], nm) ||
-      dalloc(&c->keys[1], nm) || dalloc(&c->vals[0], nm) || dalloc(&c->vals[1], nm) ||
-      dalloc(&c->us, 3 * nm) || dalloc(&c->ps, 3 * nm) || dalloc(&c->ids, nm) ||
-      dalloc(&c->counts, 3 * (c->nbuckets + 1)) || dalloc(&c->bstart, 3 * (c->nbuckets + 1)) ||
-      dalloc(&c->bprev, 3 * (c->nbuckets + 1)) || dalloc(&c->rs_low, c->nbuckets + 1) ||
-      dalloc(&c->rs_k2, nm) || dalloc(&c->rs_v2, nm) || dalloc(&c->rs_dev, 1) ||
-      dalloc(&c->hist, 512 * hb) || dalloc(&c->hist_scan, 512 * hb) ||
-      dalloc(&c->scan_tmp, c->scan_tmp_elems) || dalloc(&c->pk_partial, (size_t)N * 3 * 2048) ||
-      dalloc(&c->pk_final, 3 * 2048) || dalloc(&c->err_dev, 1)) {
+  if ((!two_mesh && dalloc(c, &c->meshC, me)) || dalloc(c, &c->meshA, me) || dalloc(c, &c->meshB, me) ||
+      dalloc(c, &c->ksq, N) ||
+      dalloc(c, &c->winv, N) || dalloc(c, &c->wforce, N) || dalloc(c, &c->kvec0, N) || dalloc(c, &c->keys[0], nm) ||
+      dalloc(c, &c->keys[1], nm) || dalloc(c, &c->vals[0], nm) || dalloc(c, &c->vals[1], nm) ||
+      dalloc(c, &c->us, 3 * nm) || dalloc(c, &c->ps, 3 * nm) || dalloc(c, &c->ids, nm) ||
+      dalloc(c, &c->counts, 3 * (c->nbuckets + 1)) || dalloc(c, &c->bstart, 3 * (c->nbuckets + 1)) ||
+      dalloc(c, &c->bprev, 3 * (c->nbuckets + 1)) || dalloc(c, &c->rs_low, c->nbuckets + 1) ||
+      dalloc(c, &c->rs_k2, nm) || dalloc(c, &c->rs_v2, nm) || dalloc(c, &c->rs_dev, 1) ||
+      dalloc(c, &c->hist, 512 * hb) || dalloc(c, &c->hist_scan, 512 * hb) ||
+      dalloc(c, &c->scan_tmp, c->scan_tmp_elems) || dalloc(c, &c->pk_partial, (size_t)N * 3 * 2048) ||
+      dalloc(c, &c->pk_final, 3 * 2048) || dalloc(c, &c->err_dev, 1)) {
     free_all(c);
     delete c;
     return PM_ENOMEM;
@@ -538,7 +561,7 @@ int pm_sync(pm_ctx* c, void* stream) {
   if (e) {
     cudaMemsetAsync(c->err_dev, 0, sizeof(int), s);
     cudaStreamSynchronize(s);
-    return (e & 2) ? PM_ETIMEOUT : PM_EKERNEL;
+    return (e & 2) ? PM_ETIMEOUT : ((e & 4) ? PM_ENONFINITE : PM_EKERNEL);
   }
   return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
 }
@@ -609,16 +632,16 @@ int pm_step_host(pm_ctx* c, uint32_t* u, float* p, uint32_t* id, float* f, int64
   if (n <= 0 || n > c->n_max || !u || !p || !id || !f || !f_valid) return PM_EINVAL;
   cudaStream_t s = S(stream);
   if (n > c->hs_cap) {
-    cudaFree(c->hs_u);
-    cudaFree(c->hs_p);
-    cudaFree(c->hs_id);
-    cudaFree(c->hs_f);
+    ctx_free(c, c->hs_u);
+    ctx_free(c, c->hs_p);
+    ctx_free(c, c->hs_id);
+    ctx_free(c, c->hs_f);
     c->hs_u = nullptr;
     c->hs_p = c->hs_f = nullptr;
     c->hs_id = nullptr;
     c->hs_cap = 0;
-    if (dalloc(&c->hs_u, 3 * n) || dalloc(&c->hs_p, 3 * n) || dalloc(&c->hs_id, n) ||
-        dalloc(&c->hs_f, 3 * n))
+    if (dalloc(c, &c->hs_u, 3 * n) || dalloc(c, &c->hs_p, 3 * n) || dalloc(c, &c->hs_id, n) ||
+        dalloc(c, &c->hs_f, 3 * n))
       return PM_ENOMEM;
     c->hs_cap = n;
   }
@@ -904,6 +927,15 @@ int pm_ic_vjp(pm_ctx* c, const float* lam_x0, const float* lam_p0, double a0, do
 }
 
 int64_t pm_launch_count(pm_ctx* c) { return valid(c) ? c->launches : -1; }
+
+int64_t pm_memory_used(pm_ctx* c) { return valid(c) ? (int64_t)c->mem_used : -1; }
+
+int pm_test_inject(pm_ctx* c, int32_t what) {
+  if (!valid(c)) return PM_ENOTINIT;
+  if (what != 0 && what != PM_INJECT_DROP_COPY) return PM_EINVAL;
+  c->inject = what;
+  return PM_OK;
+}
 
 int pm_profile_enable(pm_ctx* c, int32_t mask) {
   if (!valid(c)) return PM_ENOTINIT;

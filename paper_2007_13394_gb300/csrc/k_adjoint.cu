@@ -341,11 +341,10 @@ __global__ void k_icadj_kspace(const float2* __restrict__ a, float2* __restrict_
 
 int ensure_adj(pm_ctx* c, int64_t n) {
   if (n <= c->adj_cap) return PM_OK;
-  cudaFree(c->adj);
+  ctx_free(c, c->adj);
   c->adj = nullptr;
   c->adj_cap = 0;
-  if (cudaMalloc(&c->adj, sizeof(float) * 8 * 3 * (size_t)std::max<int64_t>(n, 1)) != cudaSuccess)
-    return PM_ENOMEM;
+  if (ctx_alloc_n(c, &c->adj, 8 * 3 * (size_t)std::max<int64_t>(n, 1)) != PM_OK) return PM_ENOMEM;
   c->adj_cap = n;
   return PM_OK;
 }

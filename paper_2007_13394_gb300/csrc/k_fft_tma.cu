@@ -17,8 +17,9 @@
 // written (by the same CTA, later) by one CTA only.
 //
 // Every wait on a copy is bounded: after kSpinLimit polls the CTA records
-// PM_ETIMEOUT's bit in the error word, waits (bounded) for its other copy in
-// flight, and returns.
+// PM_ETIMEOUT's bit in the error word, waits (bounded) for its other copies in
+// flight, and returns.  pm_test_inject exercises that path: the first CTA then skips
+// its first tile's copy (and gives up after a shorter limit).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -33,6 +34,7 @@ namespace {
 using namespace fft;
 
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kSpinLimitInjected = 1 << 12;  // a dropped copy (pm_test_inject) gives up sooner
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -59,8 +61,8 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+  for (int i = 0; i < limit; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
@@ -108,7 +110,7 @@ template <int LOGM, int TK, bool INV, int MODE>
 __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_strided_tma(
     const __grid_constant__ CUtensorMap map, float2* __restrict__ d0, float2* __restrict__ d1,
     float2* __restrict__ d2, int axis, int pc, int ntiles_z, int ntiles,
-    const float2* __restrict__ tw, KTables kt, int comp, int* __restrict__ err) {
+    const float2* __restrict__ tw, KTables kt, int comp, int* __restrict__ err, int drop) {
   using S = TmaShape<LOGM, TK, MODE>;
   constexpr int M = S::M, V = S::V, Q = M / V, NBUF = S::NBUF;
   extern __shared__ __align__(128) unsigned char smraw[];
@@ -124,7 +126,11 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     fail = 0;
   }
   __syncthreads();
+  // drop != 0 (a test injection): CTA 0 never issues its first tile's copy, so the wait on
+  // it runs out after the short limit and the CTA takes the timeout path below
+  const int limit = drop ? kSpinLimitInjected : kSpinLimit;
   auto issue = [&](int tile, int b) {
+    if (drop && blockIdx.x == 0 && tile == 0) return;
     const int outer = tile / ntiles_z, kz0 = (tile % ntiles_z) * TK;
     mbar_expect_tx(&bars[b], S::TILE_BYTES);
 #pragma unroll
@@ -155,14 +161,15 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(ahead, (it + NBUF - 1) % NBUF);  // the buffer released at the end of the last iteration
     }
-    if (!mbar_wait_bounded(&bars[b], parity[b])) fail = 1;
+    if (!mbar_wait_bounded(&bars[b], parity[b], limit)) fail = 1;
     parity[b] ^= 1u;
     __syncthreads();
     if (fail) {
       if (threadIdx.x == 0) {
         atomicOr(err, 2);
         for (int q = 1; q < NBUF; ++q)  // copies still in flight: wait for them (bounded)
-          if (tile + q * (int)gridDim.x < ntiles) mbar_wait_bounded(&bars[(it + q) % NBUF], parity[(it + q) % NBUF]);
+          if (tile + q * (int)gridDim.x < ntiles)
+            mbar_wait_bounded(&bars[(it + q) % NBUF], parity[(it + q) % NBUF], kSpinLimit);
       }
       return;
     }
@@ -260,8 +267,10 @@ int launch(pm_ctx* c, const CUtensorMap* map, float2* d0, float2* d1, float2* d2
   const int ntiles = M * ntz;
   int grid = sms * blocks_per_sm;
   if (grid > ntiles) grid = ntiles;
+  const int drop = c->inject == PM_INJECT_DROP_COPY ? 1 : 0;
+  c->inject = 0;  // one shot
   kern<<<grid, SH::THREADS, SH::SMEM, s>>>(*map, d0, d1, d2, axis, pc, ntz, ntiles, tw, kt, comp,
-                                            c->err_dev);
+                                            c->err_dev, drop);
   return PM_OK;
 }
 

@@ -146,11 +146,12 @@ int ic_build(pm_ctx* c, const float* noise, double a0, double k_fs, pm_state* st
   // amplitude tables by |n|^2 (FP64 on the host)
   const long long len = 3LL * (nc / 2) * (nc / 2) + 1;
   if (len > c->ic_amp_len || k_fs != c->ic_kfs) {
-    if (c->ic_amp) cudaFree(c->ic_amp);
-    if (c->ic_amp_nu) cudaFree(c->ic_amp_nu);
+    ctx_free(c, c->ic_amp);
+    ctx_free(c, c->ic_amp_nu);
     c->ic_amp = c->ic_amp_nu = nullptr;
-    PM_CUDA_TRY(cudaMalloc(&c->ic_amp, sizeof(float) * len));
-    PM_CUDA_TRY(cudaMalloc(&c->ic_amp_nu, sizeof(float) * len));
+    c->ic_amp_len = 0;
+    if (ctx_alloc_n(c, &c->ic_amp, (size_t)len) != PM_OK || ctx_alloc_n(c, &c->ic_amp_nu, (size_t)len) != PM_OK)
+      return PM_ENOMEM;
     c->ic_amp_len = len;
     c->ic_kfs = k_fs;
     const double A = power_amplitude(cf.omega_m, cf.h, cf.ns, cf.sigma8);

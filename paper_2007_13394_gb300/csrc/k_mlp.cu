@@ -300,12 +300,9 @@ int mlp_set(pm_ctx* c, const float* theta_host, int64_t nparam) {
   if (!c->mlp_theta) {
     const int64_t half = c->g.n / 2;
     c->mlp_ntab = 3 * half * half + 1;
-    if (cudaMalloc(&c->mlp_theta, sizeof(float) * NP) != cudaSuccess ||
-        cudaMalloc(&c->mlp_tab, sizeof(float) * c->mlp_ntab) != cudaSuccess ||
-        cudaMalloc(&c->mlp_gbin, sizeof(double) * c->mlp_ntab) != cudaSuccess ||
-        cudaMalloc(&c->mlp_dtheta, sizeof(double) * NP) != cudaSuccess ||
-        cudaMalloc(&c->mlp_adam, sizeof(float) * 2 * NP) != cudaSuccess ||
-        cudaMalloc(&c->mlp_red, sizeof(double) * 4) != cudaSuccess) {
+    if (ctx_alloc_n(c, &c->mlp_theta, NP) != PM_OK || ctx_alloc_n(c, &c->mlp_tab, c->mlp_ntab) != PM_OK ||
+        ctx_alloc_n(c, &c->mlp_gbin, c->mlp_ntab) != PM_OK || ctx_alloc_n(c, &c->mlp_dtheta, NP) != PM_OK ||
+        ctx_alloc_n(c, &c->mlp_adam, 2 * NP) != PM_OK || (!c->mlp_red && ctx_alloc_n(c, &c->mlp_red, 4) != PM_OK)) {
       mlp_free(c);
       return PM_ENOMEM;
     }
@@ -322,12 +319,12 @@ int mlp_set(pm_ctx* c, const float* theta_host, int64_t nparam) {
 }
 
 void mlp_free(pm_ctx* c) {
-  cudaFree(c->mlp_theta);
-  cudaFree(c->mlp_tab);
-  cudaFree(c->mlp_gbin);
-  cudaFree(c->mlp_dtheta);
-  cudaFree(c->mlp_adam);
-  cudaFree(c->mlp_red);
+  ctx_free(c, c->mlp_theta);
+  ctx_free(c, c->mlp_tab);
+  ctx_free(c, c->mlp_gbin);
+  ctx_free(c, c->mlp_dtheta);
+  ctx_free(c, c->mlp_adam);
+  ctx_free(c, c->mlp_red);
   c->mlp_theta = c->mlp_tab = c->mlp_adam = nullptr;
   c->mlp_gbin = c->mlp_dtheta = c->mlp_red = nullptr;
   c->mlp_on = false;
@@ -443,14 +440,14 @@ int pm_displacement_loss(pm_ctx* c, const uint32_t* u, const uint32_t* id, const
   if (!c || c->magic != kMagic) return PM_ENOTINIT;
   if (n <= 0 || n > c->n_max || !u || !u_ref || !lam_x || !loss || species < 1 || species > 3)
     return PM_EINVAL;
-  if (!c->mlp_red && cudaMalloc(&c->mlp_red, sizeof(double) * 4) != cudaSuccess) return PM_ENOMEM;
+  if (!c->mlp_red && ctx_alloc_n(c, &c->mlp_red, 4) != PM_OK) return PM_ENOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // canonical copy of the reference positions in the adjoint scratch
   if (n > c->adj_cap) {
-    cudaFree(c->adj);
+    ctx_free(c, c->adj);
     c->adj = nullptr;
     c->adj_cap = 0;
-    if (cudaMalloc(&c->adj, sizeof(float) * 8 * 3 * (size_t)n) != cudaSuccess) return PM_ENOMEM;
+    if (ctx_alloc_n(c, &c->adj, 8 * 3 * (size_t)n) != PM_OK) return PM_ENOMEM;
     c->adj_cap = n;
   }
   uint32_t* ref_c = reinterpret_cast<uint32_t*>(c->adj);

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
   __syncthreads();
   const float fscale = 1.0f / (float)(1u << shift);
   const uint32_t fmask = (1u << shift) - 1u;
-  bool bad = false;
+  bool bad = false, nonfinite = false;
   for (; i < hi; i += kFd4Threads) {
     const uint32_t inext = i + kFd4Threads;
     uint32_t nu[3] = {0u, 0u, 0u}, nid = 0u;
@@ -420,6 +420,8 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
         }
       }
       const float F[3] = {-inv12h * Fx, -inv12h * Fy, -inv12h * Fz};
+      // a NaN or infinity in the force or the incoming momentum poisons the sum
+      if (!isfinite(F[0] + F[1] + F[2] + cp[0] + cp[1] + cp[2])) nonfinite = true;
       if (perm) {  // force in the caller's order
         const uint32_t j = perm[i];
 #pragma unroll
@@ -451,6 +453,7 @@ __global__ void __launch_bounds__(kFd4Threads) k_readout_fd4_kick(
     cid = nid;
   }
   if (bad) atomicOr(err, 1);
+  if (nonfinite) atomicOr(err, 4);
 }
 
 // First half kick with the cached force, drift in fixed point, next sort key.
@@ -466,16 +469,18 @@ __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ 
                                   const float* __restrict__ f, int64_t n, float K1, float dscale,
                                   int shift, int ntl, uint32_t* __restrict__ keys,
                                   uint32_t* __restrict__ cnt3, long long nb1, const uint32_t* __restrict__ bprev,
-                                  uint32_t* __restrict__ low, uint32_t* __restrict__ flags) {
+                                  uint32_t* __restrict__ low, uint32_t* __restrict__ flags, int* __restrict__ err) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = i < n;
   uint32_t key = 0xffffffffu, cat = 0xffffffffu, ko = 0xffffffffu;
   uint32_t flag = 0u;
   if (ok) {
     uint32_t uu[3], u0[3];
+    float chk = 0.0f;  // a NaN or infinity in p or f poisons the sum
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const float pv = __fmaf_rn(K1, f[d * n + i], p[d * n + i]);
+      chk += pv;
       p[d * n + i] = pv;
       // u += rne(Delta p 2^32 / L), modulo 2^32; the 32-bit conversion (same rounding)
       // whenever the step fits, the 64-bit one (FP64 pipe) only for steps of 2^31 or more
@@ -485,6 +490,7 @@ __global__ void k_kick_drift_keys(uint32_t* __restrict__ u, float* __restrict__ 
     }
     key = tile_key(uu[0], uu[1], uu[2], shift, ntl);
     keys[i] = key;
+    if (!isfinite(chk)) atomicOr(err, 4);
     if constexpr (RESORT) {
       const uint32_t k0 = tile_key(u0[0], u0[1], u0[2], shift, ntl);
       const bool in_range = (uint32_t)i >= bprev[k0] && (uint32_t)i < bprev[k0 + 1];
@@ -609,10 +615,10 @@ void kick_drift_keys(pm_ctx* c, uint32_t* u, float* p, const float* f, int64_t n
   const unsigned grid = (unsigned)((n + 255) / 256);
   if (resort)
     k_kick_drift_keys<true><<<grid, 256, 0, s>>>(u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0],
-                                                  c->counts, nb1, c->bprev, c->rs_low, c->rs_dev);
+                                                  c->counts, nb1, c->bprev, c->rs_low, c->rs_dev, c->err_dev);
   else
     k_kick_drift_keys<false><<<grid, 256, 0, s>>>(u, p, f, n, K1, dscale, 32 - c->g.logn, c->ntl, c->keys[0],
-                                                   c->counts, nb1, nullptr, nullptr, nullptr);
+                                                   c->counts, nb1, nullptr, nullptr, nullptr, c->err_dev);
 }
 
 void repack_real(pm_ctx* c, const Geom& g, const float* src, int sp, float* dst, int dp,

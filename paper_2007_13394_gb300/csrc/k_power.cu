@@ -120,7 +120,7 @@ int power_weight(pm_ctx* c, int nbins, const double* dL_dP, cudaStream_t s) {
     for (int b = 0; b < nbins; ++b)
       if (nb[b] > 0) cw[b] = (float)(2.0 * dL_dP[b] * V / (n3 * n3 * rho_bar * rho_bar * (double)nb[b]));
   }
-  if (!c->pk_w && cudaMalloc(&c->pk_w, sizeof(float) * kMaxBins) != cudaSuccess) return PM_ENOMEM;
+  if (!c->pk_w && ctx_alloc_n(c, &c->pk_w, kMaxBins) != PM_OK) return PM_ENOMEM;
   PM_CUDA_TRY(cudaMemcpyAsync(c->pk_w, cw.data(), sizeof(float) * nbins, cudaMemcpyHostToDevice, s));
   LaunchScope L(c, s, K_POWER_BIN);
   k_power_weight<<<g.n, kPowThreads, 0, s>>>(c->meshA, g.n, g.pc, nbins, c->winv, c->pk_w);

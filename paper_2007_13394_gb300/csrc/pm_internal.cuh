@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/pm.h"
@@ -176,6 +177,11 @@ struct pm_ctx {
   float* mlp_adam = nullptr;      // Adam first and second moments, 2 x PM_MLP_NPARAM
   double* mlp_red = nullptr;      // device scalars of the displacement loss reductions
   double force_a = 1.0;           // scale factor of pm_force / pm_potential / pm_force_vjp
+  // device memory held, by allocation, against cfg.mem_limit
+  std::unordered_map<void*, size_t> allocs;
+  size_t mem_used = 0;
+  // pending test injection (pm_test_inject), consumed by the launch it targets
+  int inject = 0;
   // instrumentation
   int64_t launches = 0;
   uint32_t prof = 0;  // bit k: time kernel kind k
@@ -198,6 +204,15 @@ struct LaunchScope {
   LaunchScope(pm_ctx* ctx, cudaStream_t st, int k);
   ~LaunchScope();
 };
+
+// Device memory of a context, charged against cfg.mem_limit (0: no limit): PM_ENOMEM without
+// calling cudaMalloc when the limit would be passed, or when cudaMalloc fails (*p = NULL).
+int ctx_alloc(pm_ctx* c, void** p, size_t bytes);
+void ctx_free(pm_ctx* c, void* p);  // NULL is a no-op
+template <class T>
+int ctx_alloc_n(pm_ctx* c, T** p, size_t count) {
+  return ctx_alloc(c, reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
 
 // host launch helpers implemented in the .cu files
 int sort_particles(pm_ctx* c, const uint32_t* u, int64_t n, cudaStream_t s);  // keys + radix -> vals

@@ -18,6 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpmnu.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
+PM_ENONFINITE = -7
+PM_INJECT_DROP_COPY = 1
 SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
 MLP_HIDDEN, MLP_NPARAM = 64, 4417
 FLAG_TWO_MESH, FLAG_SPECTRAL_KERNEL, FLAG_MLP_TENSOR, FLAG_KSPACE_GRADIENT = 1, 2, 4, 8
@@ -37,7 +39,7 @@ class Config(ctypes.Structure):
         ("n_eff", ctypes.c_double), ("n_nu", ctypes.c_int32), ("pad0", ctypes.c_int32),
         ("m_nu", ctypes.c_double * 3), ("a_ini_ode", ctypes.c_double), ("n_max", ctypes.c_int64),
         ("ns", ctypes.c_double), ("sigma8", ctypes.c_double), ("flags", ctypes.c_uint32),
-        ("pad1", ctypes.c_int32),
+        ("pad1", ctypes.c_int32), ("mem_limit", ctypes.c_int64),
     ]
 
 
@@ -104,6 +106,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "pm_mlp_adam": (ctypes.c_int, [vp, vp, i64, d, d, d, d, i64, vp]),
         "pm_displacement_loss": (ctypes.c_int, [vp, vp, vp, vp, vp, i64, i32, vp, dp, vp]),
         "pm_launch_count": (i64, [vp]),
+        "pm_memory_used": (i64, [vp]),
+        "pm_test_inject": (ctypes.c_int, [vp, i32]),
         "pm_profile_enable": (ctypes.c_int, [vp, i32]),
         "pm_profile_read": (ctypes.c_int, [vp, i32, dp, ctypes.POINTER(i64), i32]),
         "pm_kernel_kinds": (i32, []),
@@ -149,6 +153,7 @@ class RunConfig:
     ns: float = 0.965
     sigma8: float = 0.81
     flags: int = 0
+    mem_limit: int = 0
     extra: dict = field(default_factory=dict)
 
     def n_cdm(self) -> int:
@@ -173,6 +178,7 @@ class RunConfig:
         c.n_max = self.n_max or self.n_particles()
         c.ns, c.sigma8 = self.ns, self.sigma8
         c.flags = self.flags
+        c.mem_limit = self.mem_limit
         return c
 
 
@@ -541,6 +547,14 @@ class ParticleMesh:
                                              _stream()),
                "pm_displacement_loss")
         return out.value, lam
+
+    def memory_used(self):
+        """Bytes of device memory the context holds (checked against RunConfig.mem_limit)."""
+        return int(self.lib.pm_memory_used(self.h))
+
+    def test_inject(self, what):
+        """Arm a one-shot failure of the next launch of the selected kind (PM_INJECT_*)."""
+        _check(self.lib.pm_test_inject(self.h, what), "pm_test_inject")
 
     def launch_count(self):
         return int(self.lib.pm_launch_count(self.h))
