@@ -197,6 +197,26 @@ def force(u, mass, n, box, omega_m0, kfactor=None, kernel="fd4"):
     return np.stack([readout(u, force_mesh(phi, box, n, j, kernel), n) for j in range(3)])
 
 
+def force_at(u, mass, n, box, omega_m0, pick, kernel="fd4", workers=None):
+    """The PM force of :func:`force` read out only at the particles ``pick`` (3, len(pick)).
+
+    The mesh steps are the same definitions -- paint of every particle, phi_k, F_j =
+    IFFT[-i D(k_j) phi_k] -- with the transforms on ``workers`` threads of scipy.fft (a
+    library FFT like numpy's; the thread count changes only the speed).  For sampled
+    checks on meshes where reading out every particle would be slow."""
+    from scipy import fft as sfft
+    phi = sfft.rfftn(paint(u, mass, n), workers=workers)
+    phi *= green_half(n, box, omega_m0, kernel)
+    dfull, dhalf = gradient_kernel(n, box, kernel)
+    up = np.asarray(u)[:, pick]
+    out = []
+    for j, kj in enumerate((dfull[:, None, None], dfull[None, :, None], dhalf[None, None, :])):
+        fj = sfft.irfftn(-1j * kj * phi, s=(n, n, n), axes=(0, 1, 2), workers=workers) * n ** 3
+        out.append(readout(up, fj, n))
+        del fj
+    return np.stack(out)
+
+
 # --------------------------------------------------------------- kick / drift
 def drift(u, p, delta, box):
     """u_d <- (u_d + rne(Delta p_d 2^32 / L)) mod 2^32 (exact periodicity)."""

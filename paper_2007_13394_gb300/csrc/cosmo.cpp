@@ -93,6 +93,7 @@ int validate_config(const pm_config& c) {
   if (c.flags & ~(uint32_t)(PM_FLAG_TWO_MESH | PM_FLAG_SPECTRAL_KERNEL | PM_FLAG_MLP_TENSOR |
                            PM_FLAG_KSPACE_GRADIENT))
     return PM_EINVAL;
+  if (c.mem_limit < 0) return PM_EINVAL;
   for (int i = 0; i < c.n_nu; ++i)
     if (!(c.m_nu[i] >= 0.0) || !std::isfinite(c.m_nu[i])) return PM_EINVAL;
   if (c.nsites > 0) {

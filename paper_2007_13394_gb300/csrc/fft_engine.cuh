@@ -237,6 +237,77 @@ __device__ __forceinline__ void run_stages_reg(float2 (&v)[V], int j, float2* sm
   if constexpr (!LAST) run_stages_reg<M, NS * R, INV, OFF + (NS > 1 ? (V / R) * (R - 1) : 0), NTW, V>(v, j, sm, cs, w);
 }
 
+// Global loads of the FFT passes: the default path, or ld.global.cg (L2 only), which the
+// fused (z, y) passes need because they read lines that other SMs wrote during the launch.
+template <bool CG>
+__device__ __forceinline__ float2 gload(const float2* p) {
+  if constexpr (CG) {
+    return __ldcg(p);
+  } else {
+    return *p;
+  }
+}
+
+// z pass, real -> complex, of one row: N reals read as M = N/2 complex values, held by
+// M/16 threads (j = 0 .. M/16 - 1) with 16 values each; ls is the row's shared-memory line
+// (M + M/16 + 2 float2).  Writes the N/2 + 1 modes k = 0 .. M over the row in place.
+// ok = false: the thread takes part in the barriers only.
+template <int LOGN, bool WARP, bool CG>
+__device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
+                                          const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16;
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
+  run_stages<M, N, 1, false, 16, WARP>(v, j, ls, 1, tw);
+#pragma unroll
+  for (int s = 0; s < 16; ++s) ls[padi(j + s * TPL)] = v[s];
+  line_sync<WARP>();
+  if (ok) {
+    for (int k = j; k <= M; k += TPL) {
+      float2 zk = ls[padi(k & (M - 1))];
+      float2 zm = cconj(ls[padi((M - k) & (M - 1))]);
+      float2 e = cscale(cadd(zk, zm), 0.5f);
+      float2 o = cscale(csub(zk, zm), 0.5f);
+      float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
+      float2 wo = cmul(w, o);
+      rp[k] = make_float2(e.x + wo.y, e.y - wo.x);  // e - i w o
+    }
+  }
+}
+
+// z pass, complex -> real, of one row in place (the inverse of z_r2c_row, unnormalised).
+template <int LOGN, bool WARP, bool CG>
+__device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
+                                          const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int k = j + s * TPL;
+    ls[padi(k)] = ok ? gload<CG>(rp + k) : make_float2(0.f, 0.f);
+  }
+  if (j == 0) ls[padi(M)] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
+  line_sync<WARP>();
+  float2 v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int k = j + s * TPL;
+    float2 xk = ls[padi(k)];
+    float2 xm = cconj(ls[padi(M - k)]);
+    float2 e = cadd(xk, xm);
+    float2 d = csub(xk, xm);
+    float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
+    float2 wd = cmul(w, d);
+    v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
+  }
+  line_sync<WARP>();
+  run_stages<M, N, 1, true, 16, WARP>(v, j, ls, 1, tw);
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
+  }
+}
+
 // Fused epilogue / prologue of the x pass.
 struct KTables {
   const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)

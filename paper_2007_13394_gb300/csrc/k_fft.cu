@@ -48,26 +48,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_r2c(float2* __restrict_
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  const bool ok = row < nrows;
-  float2* rp = data + row * pc;
-  float2 v[16];
-#pragma unroll
-  for (int s = 0; s < 16; ++s) v[s] = ok ? rp[j + s * TPL] : make_float2(0.f, 0.f);
-  float2* ls = sm + line * LS;
-  run_stages<M, N, 1, false, 16, WARP>(v, j, ls, 1, tw);
-#pragma unroll
-  for (int s = 0; s < 16; ++s) ls[padi(j + s * TPL)] = v[s];
-  line_sync<WARP>();
-  if (!ok) return;
-  for (int k = j; k <= M; k += TPL) {
-    float2 zk = ls[padi(k & (M - 1))];
-    float2 zm = cconj(ls[padi((M - k) & (M - 1))]);
-    float2 e = cscale(cadd(zk, zm), 0.5f);
-    float2 o = cscale(csub(zk, zm), 0.5f);
-    float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
-    float2 wo = cmul(w, o);
-    rp[k] = make_float2(e.x + wo.y, e.y - wo.x);  // e - i w o
-  }
+  z_r2c_row<LOGN, WARP, false>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 // z pass, complex -> real, in place.
@@ -80,33 +61,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  const bool ok = row < nrows;
-  float2* rp = data + row * pc;
-  float2* ls = sm + line * LS;
-#pragma unroll
-  for (int s = 0; s < 16; ++s) {
-    const int k = j + s * TPL;
-    ls[padi(k)] = ok ? rp[k] : make_float2(0.f, 0.f);
-  }
-  if (j == 0) ls[padi(M)] = ok ? rp[M] : make_float2(0.f, 0.f);
-  line_sync<WARP>();
-  float2 v[16];
-#pragma unroll
-  for (int s = 0; s < 16; ++s) {
-    const int k = j + s * TPL;
-    float2 xk = ls[padi(k)];
-    float2 xm = cconj(ls[padi(M - k)]);
-    float2 e = cadd(xk, xm);
-    float2 d = csub(xk, xm);
-    float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
-    float2 wd = cmul(w, d);
-    v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
-  }
-  line_sync<WARP>();
-  run_stages<M, N, 1, true, 16, WARP>(v, j, ls, 1, tw);
-  if (!ok) return;
-#pragma unroll
-  for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
+  z_c2r_row<LOGN, WARP, false>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 

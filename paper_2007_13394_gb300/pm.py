@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpmnu.so")
 
 PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_EKERNEL, PM_ETIMEOUT, PM_ENOTINIT = 0, -1, -2, -3, -4, -5, -6
 PM_ENONFINITE = -7
+PM_FLAG_TWO_MESH, PM_FLAG_SPECTRAL_KERNEL, PM_FLAG_MLP_TENSOR, PM_FLAG_KSPACE_GRADIENT = 1, 2, 4, 8
 PM_INJECT_DROP_COPY = 1
 SPECIES_CDM, SPECIES_NU, SPECIES_ALL = 1, 2, 3
 MLP_HIDDEN, MLP_NPARAM = 64, 4417

@@ -197,37 +197,6 @@ def test_gpu_ic_then_steps_conserve_momentum(pm):
     assert net < 1e-5 * np.abs(f * m).sum(axis=1).max()
 
 
-@pytest.mark.slow
-def test_full_size_benchmark_force_on_sampled_particles(pm):
-    """At the benchmark size (512^3 mesh, 256^3 + 32^3 x 70 particles), the GPU force at 4096
-    sampled particles against the oracle's FP64 mesh force read out at the same particles."""
-    from paper_2007_13394_gb300 import workloads
-    cfg = workloads.cfg2()
-    ctx = pm.ParticleMesh(cfg)
-    noise = torch.from_numpy(inputs.white_noise(cfg.nc, seed=1)).cuda()
-    st = ctx.ic(noise, 0.01, k_fs=workloads.free_streaming_k(cfg, 0.01))
-    for (a, ah, b) in workloads.schedule_paper(25)[:3]:
-        ctx.step(st, a, ah, b)
-    F = ctx.force(st["u"], st["id"])
-    ctx.sync()
-    u = pm.to_u32(st["u"])
-    ids = pm.to_u32(st["id"])
-    Fg = F.double().cpu().numpy()
-    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
-    _, _, m_shell = onu.shell_table(cfg.nshell, list(cfg.m_nu))
-    mc, mn = onu.species_masses(cfg.nmesh, cfg.nc, cfg.nsites, cfg.nshell, cfg.nfib, bg.omega_c,
-                                bg.omega_nu_poisson, m_shell)
-    mass = onu.particle_masses(cfg.n_cdm(), cfg.n_nu(), cfg.nshell, cfg.nfib, mc, mn)[ids]
-    phi = opm.potential_k(opm.paint(u, mass, cfg.nmesh), cfg.box, bg.omega_m0)
-    rng = np.random.default_rng(0)
-    pick = rng.choice(u.shape[1], 4096, replace=False)
-    ref = np.stack([opm.readout(u[:, pick], opm.force_mesh(phi, cfg.box, cfg.nmesh, j), cfg.nmesh)
-                    for j in range(3)])
-    got = Fg[:, pick]
-    rel = np.sqrt(((got - ref) ** 2).sum() / (ref ** 2).sum())
-    assert rel < 1e-5, rel
-
-
 def test_checkpoint_resume_is_bit_identical(pm, tmp_path):
     """Run 4 steps; or run 2, save, load into fresh arrays, run 2 more: identical state."""
     from paper_2007_13394_gb300 import workloads

@@ -426,3 +426,18 @@ def test_cross_power_linearity_identity():
     _, Pmm, _ = pm.power_spectrum(rm, None, L, 12)
     np.testing.assert_allclose(Pmm, (1 - fnu) ** 2 * Pcc + 2 * fnu * (1 - fnu) * Pcn + fnu ** 2 * Pnn,
                                rtol=1e-11)
+
+
+def test_force_at_equals_the_full_force_at_the_picked_particles():
+    """The sampled oracle force (scipy transforms, readout at a subset) is the full force
+    restricted to that subset."""
+    rng = np.random.default_rng(11)
+    n, box = 32, 100.0
+    u = rng.integers(0, 2 ** 32, size=(3, 500), dtype=np.uint64).astype(np.uint32)
+    mass = rng.uniform(0.5, 2.0, 500)
+    pick = rng.choice(500, 37, replace=False)
+    full = pm.force(u, mass, n, box, 0.31)
+    for kernel in pm.KERNELS:
+        full = pm.force(u, mass, n, box, 0.31, kernel=kernel)
+        got = pm.force_at(u, mass, n, box, 0.31, pick, kernel=kernel, workers=2)
+        np.testing.assert_allclose(got, full[:, pick], rtol=1e-12, atol=1e-14 * np.abs(full).max())
