@@ -66,13 +66,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
 
 
 
-// Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK).
-// 64 registers a thread: two 512-thread CTAs (or four of 256) resident per SM
-template <int LOGM, int TK, bool INV, int EPI, int PRO>
-__global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) / 16)) k_fft_strided(
+// Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK),
+// V values a thread.  MINB CTAs per SM: 1024 threads in all (64 registers a thread) by
+// default.
+template <int LOGM, int TK, bool INV, int EPI, int PRO, int V = 16,
+          int MINB = 1024 / (TK * (1 << LOGM) / V)>
+__global__ void __launch_bounds__(TK*(1 << LOGM) / V, MINB) k_fft_strided(
     const float2* __restrict__ src, float2* __restrict__ dst, int axis, int pc, int ntiles_z,
     const float2* __restrict__ tw, KTables kt, int comp) {
-  constexpr int M = 1 << LOGM, Q = M / 16;
+  constexpr int M = 1 << LOGM, Q = M / V;
   extern __shared__ float2 sm[];
   const int c = threadIdx.x % TK, j = threadIdx.x / TK;
   const int outer = blockIdx.x / ntiles_z;
@@ -80,25 +82,25 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
   const bool ok = kz <= M / 2;
   const long long stride = axis == 1 ? (long long)pc : (long long)M * pc;
   const long long base = (axis == 1 ? (long long)outer * M * pc : (long long)outer * pc) + kz;
-  float2 v[16];
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 16; ++s)
+  for (int s = 0; s < V; ++s)
     v[s] = ok ? src[base + (long long)(j + s * Q) * stride] : make_float2(0.f, 0.f);
   if constexpr (PRO == PRO_GRAD) {  // v *= -i k_comp; x pass: element index is kx, outer is ky
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
+    for (int s = 0; s < V; ++s) {
       const int kx = j + s * Q;
       const float kk = comp == 0 ? __ldg(kt.kvec0 + kx)
                                  : (comp == 1 ? __ldg(kt.kvec0 + outer) : __ldg(kt.kvec0 + kz));
       v[s] = make_float2(kk * v[s].y, -kk * v[s].x);
     }
   }
-  run_stages<M, M, 1, INV>(v, j, sm + c, TK, tw);
+  run_stages<M, M, 1, INV, V>(v, j, sm + c, TK, tw);
   if constexpr (EPI == EPI_GREEN || EPI == EPI_POT) {
     const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
     const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
+    for (int s = 0; s < V; ++s) {
       const int kx = j + s * Q;
       const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
       float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
@@ -107,10 +109,10 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
       v[s] = cscale(v[s], g);
     }
   }
-  if constexpr (EPI == EPI_POT) run_stages<M, M, 1, true>(v, j, sm + c, TK, tw);
+  if constexpr (EPI == EPI_POT) run_stages<M, M, 1, true, V>(v, j, sm + c, TK, tw);
   if (!ok) return;
 #pragma unroll
-  for (int s = 0; s < 16; ++s) dst[base + (long long)(j + s * Q) * stride] = v[s];
+  for (int s = 0; s < V; ++s) dst[base + (long long)(j + s * Q) * stride] = v[s];
 }
 
 // Fused x pass of the force: forward x FFT of one column tile, Green's function,
@@ -191,19 +193,23 @@ void launch_x_fused(float2* a, float2* b, float2* cz, int pc, const float2* tw, 
   k_fft_x_fused<LOGM, TK><<<(unsigned)(M * ntz), threads, smem, s>>>(a, b, cz, pc, ntz, tw, kt);
 }
 
-template <int LOGM>
-constexpr int tk_for() {
-  return LOGM >= 10 ? 8 : 16;
-}
+// Shape of the classic strided kernel: TK columns a CTA, V values a thread, MINB CTAs per SM.
+template <int LOGM, int EPI>
+struct StridedShape {
+  static constexpr int TK = LOGM >= 10 ? 8 : 16;
+  static constexpr int V = 16;
+  static constexpr int MINB = 1024 / (TK * (1 << LOGM) / V);
+};
 
 template <int LOGM, bool INV, int EPI, int PRO>
 void launch_strided(const float2* src, float2* dst, int axis, int pc, const float2* tw,
                     const KTables& kt, int comp, cudaStream_t s) {
-  constexpr int M = 1 << LOGM, TK = tk_for<LOGM>();
-  constexpr int threads = TK * M / 16;
+  using SS = StridedShape<LOGM, EPI>;
+  constexpr int M = 1 << LOGM, TK = SS::TK;
+  constexpr int threads = TK * M / SS::V;
   const int ntz = (M / 2 + 1 + TK - 1) / TK;
   const size_t smem = sizeof(float2) * (size_t)(M + M / 16 + 1) * TK;
-  auto kern = k_fft_strided<LOGM, TK, INV, EPI, PRO>;
+  auto kern = k_fft_strided<LOGM, TK, INV, EPI, PRO, SS::V, SS::MINB>;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
