@@ -155,7 +155,14 @@ def source_digest(files=None):
 # from one ncu capture of the current build, keyed by (kernel kind, workload): (per-launch
 # bytes as a function of the timed steps, digest, the source files that define the kernel,
 # where the capture is summarised).  Reported only while those files hash to the digest.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # cfg3: the y passes (forward 34.43 + 34.89 GB, inverse 34.43 + 34.37 GB: their mean per
+    # launch, as the kind's launches alternate) and the x pass of the potential
+    ("fft_y", "cfg3"): (lambda k: 69.06e9, "0ebe6bcaa581", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
+                        "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2048^3 y passes, cfg3 step"),
+    ("fft_x_potential", "cfg3"): (lambda k: 74.01e9, "0ebe6bcaa581", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
+                                  "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2048^3 x pass, cfg3 step"),
+}
 
 
 def dist_setup(args):
@@ -324,7 +331,9 @@ def e2e_host(ctx, st, sched, base, n, k_e2e):
     import torch
     pinned = {k: torch.empty(st[k].shape, dtype=st[k].dtype, pin_memory=True) for k in ("u", "p", "id", "f")}
     for k, v in pinned.items():
-        v.copy_(st[k])
+        # a byte-view copy: torch's typed copy of an int32 array of more than 2^31 elements
+        # into pinned memory was measured at 22 GB/s, and later host-buffer steps ran slower
+        v.view(torch.uint8).copy_(st[k].view(torch.uint8))
     fv = st["f_valid"]
     for k in ("u", "p", "id", "f"):
         st[k] = None
