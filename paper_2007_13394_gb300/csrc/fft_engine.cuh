@@ -311,7 +311,8 @@ __device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int 
 // Fused epilogue / prologue of the x pass.
 struct KTables {
   const float* ksq;    // k_n^2, n in [0, N) (signed wavenumber of index n)
-  const float* winv;   // per-axis factor of the Green's function (1, or 1 / sinc^4(pi n_s / N))
+  const float* winv;   // per-axis factor of the Green's function, 1 / sinc^4(pi n_s / N) for the
+                       // deconvolved spectral kernel; null: all factors 1 (the default kernel)
   const float* kvec0;  // gradient kernel D(k_n), 0 on the Nyquist index
   float gcoef;         // -1.5 Omega_m0 / N^3
   const float* mtab;   // learned factor by |n|^2 (n signed indices), null: plain kernel

@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict_
 // Strided c2c pass along y (axis = 1) or x (axis = 0) for kz columns [kz0, kz0 + TK),
 // V values a thread.  MINB CTAs per SM: 1024 threads in all (64 registers a thread) by
 // default.
+// WIN: the Green's function's per-axis window factors are loaded (false: all 1, skipped).
 template <int LOGM, int TK, bool INV, int EPI, int PRO, int V = 16,
-          int MINB = 1024 / (TK * (1 << LOGM) / V)>
+          int MINB = 1024 / (TK * (1 << LOGM) / V), bool WIN = true>
 __global__ void __launch_bounds__(TK*(1 << LOGM) / V, MINB) k_fft_strided(
     const float2* __restrict__ src, float2* __restrict__ dst, int axis, int pc, int ntiles_z,
     const float2* __restrict__ tw, KTables kt, int comp) {
@@ -97,13 +98,17 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / V, MINB) k_fft_strided(
   }
   run_stages<M, M, 1, INV, V>(v, j, sm + c, TK, tw);
   if constexpr (EPI == EPI_GREEN || EPI == EPI_POT) {
-    const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
-    const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+    const float wy = WIN ? __ldg(kt.winv + outer) : 1.0f, ky2 = __ldg(kt.ksq + outer);
+    const float wz = !ok ? 0.f : (WIN ? __ldg(kt.winv + kz) : 1.0f), kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+    const float kf2 = __ldg(kt.ksq + 1);  // k_F^2
 #pragma unroll
     for (int s = 0; s < V; ++s) {
       const int kx = j + s * Q;
-      const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
-      float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
+      const int nx = kx < M / 2 ? kx : kx - M;  // signed index: k_x^2 = k_F^2 n_x^2, no table load
+      const float k2 = kf2 * (float)(nx * nx) + ky2 + kz2;
+      // fast division (2 ulp): the IEEE divide's extra instructions and registers cost 15 % of
+      // this issue-bound pass at 2048^3, for a 2e-7 relative change of phi_k
+      float g = __fdividef(kt.gcoef * (WIN ? __ldg(kt.winv + kx) : 1.0f) * wy * wz, k2);
       if (k2 == 0.0f) g = 0.0f;
       if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
       v[s] = cscale(v[s], g);
@@ -140,13 +145,14 @@ __global__ void __launch_bounds__(TK*(1 << LOGM) / 16, 1024 / (TK * (1 << LOGM) 
     v[s] = ok ? a[base + (long long)(j + s * Q) * stride] : make_float2(0.f, 0.f);
   run_stages<M, M, 1, false>(v, j, work + c, TK, tw);
   {
-    const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
-    const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+    const bool win = kt.winv != nullptr;  // null: unit window (no loads)
+    const float wy = win ? __ldg(kt.winv + outer) : 1.0f, ky2 = __ldg(kt.ksq + outer);
+    const float wz = !ok ? 0.f : (win ? __ldg(kt.winv + kz) : 1.0f), kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
       const int kx = j + s * Q;
       const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
-      float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
+      float g = kt.gcoef * (win ? __ldg(kt.winv + kx) : 1.0f) * wy * wz / k2;
       if (k2 == 0.0f) g = 0.0f;
       if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
       v[s] = cscale(v[s], g);
@@ -209,11 +215,14 @@ void launch_strided(const float2* src, float2* dst, int axis, int pc, const floa
   constexpr int threads = TK * M / SS::V;
   const int ntz = (M / 2 + 1 + TK - 1) / TK;
   const size_t smem = sizeof(float2) * (size_t)(M + M / 16 + 1) * TK;
-  auto kern = k_fft_strided<LOGM, TK, INV, EPI, PRO, SS::V, SS::MINB>;
-  static bool attr = false;
-  if (!attr) {
+  constexpr bool GREEN = EPI == EPI_GREEN || EPI == EPI_POT;  // only these read the window
+  const int w = (GREEN && kt.winv) ? 1 : 0;
+  auto kern = w ? k_fft_strided<LOGM, TK, INV, EPI, PRO, SS::V, SS::MINB, GREEN>
+                : k_fft_strided<LOGM, TK, INV, EPI, PRO, SS::V, SS::MINB, false>;
+  static bool attr[2] = {false, false};
+  if (!attr[w]) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
+    attr[w] = true;
   }
   kern<<<(unsigned)(M * ntz), threads, smem, s>>>(src, dst, axis, pc, ntz, tw, kt, comp);
 }
@@ -284,7 +293,9 @@ void strided(pm_ctx* c, const Geom& g, const float2* src, float2* dst, int axis,
 KTables ktables(pm_ctx* c, const Geom& g) {
   KTables kt;
   kt.ksq = c->ksq;
-  kt.winv = c->wforce;
+  // the per-axis window factors of the Green's function: all 1 for the default kernel,
+  // where the passes skip them (null), 1 / sinc^4 for the deconvolved spectral one
+  kt.winv = (c->cfg.flags & PM_FLAG_SPECTRAL_KERNEL) ? c->wforce : nullptr;
   kt.kvec0 = c->kvec0;
   double nn = (double)g.n;
   kt.gcoef = (float)(-1.5 * c->cosmo.omega_m0 / (nn * nn * nn));

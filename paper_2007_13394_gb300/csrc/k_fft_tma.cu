@@ -106,7 +106,8 @@ struct TmaShape {
   static constexpr size_t SMEM = NBUF * BUF_BYTES + (WORK_IN_TILE ? 0 : WORK_BYTES);
 };
 
-template <int LOGM, int TK, bool INV, int MODE>
+// WIN: the Green's function's per-axis window factors are loaded (false: all 1, skipped).
+template <int LOGM, int TK, bool INV, int MODE, bool WIN>
 __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_strided_tma(
     const __grid_constant__ CUtensorMap map, float2* __restrict__ d0, float2* __restrict__ d1,
     float2* __restrict__ d2, int axis, int pc, int ntiles_z, int ntiles,
@@ -194,13 +195,14 @@ __global__ void __launch_bounds__(TmaShape<LOGM, TK, MODE>::THREADS, 2) k_fft_st
     }
     run_stages_reg<M, 1, INV, 0, NTW, V>(v, j, work + c, TK, twr);
     if constexpr (MODE == MODE_GREEN || MODE == MODE_FUSED || MODE == MODE_POT) {
-      const float wy = __ldg(kt.winv + outer), ky2 = __ldg(kt.ksq + outer);
-      const float wz = ok ? __ldg(kt.winv + kz) : 0.f, kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
+      const float wy = WIN ? __ldg(kt.winv + outer) : 1.0f, ky2 = __ldg(kt.ksq + outer);
+      const float wz = !ok ? 0.f : (WIN ? __ldg(kt.winv + kz) : 1.0f), kz2 = ok ? __ldg(kt.ksq + kz) : 0.f;
 #pragma unroll
       for (int s = 0; s < V; ++s) {
         const int kx = j + s * Q;
         const float k2 = __ldg(kt.ksq + kx) + ky2 + kz2;
-        float g = kt.gcoef * __ldg(kt.winv + kx) * wy * wz / k2;
+        // fast division (2 ulp), as in the classic passes
+        float g = kt.gcoef * (WIN ? __ldg(kt.winv + kx) : 1.0f) * wy * wz / k2;
         if (k2 == 0.0f) g = 0.0f;
         if (kt.mtab && ok) g *= __ldg(kt.mtab + nsq_index<M>(kx, outer, kz));
         v[s] = cscale(v[s], g);
@@ -252,20 +254,22 @@ int launch(pm_ctx* c, const CUtensorMap* map, float2* d0, float2* d1, float2* d2
   constexpr int TK = tk_tma<LOGM>();
   using SH = TmaShape<LOGM, TK, MODE>;
   constexpr int M = SH::M;
-  auto kern = k_fft_strided_tma<LOGM, TK, INV, MODE>;
-  static int blocks_per_sm = 0;
-  if (blocks_per_sm == 0) {
+  constexpr bool GREEN = MODE == MODE_GREEN || MODE == MODE_FUSED || MODE == MODE_POT;  // read the window
+  const int w = (GREEN && kt.winv) ? 1 : 0;
+  auto kern = w ? k_fft_strided_tma<LOGM, TK, INV, MODE, GREEN> : k_fft_strided_tma<LOGM, TK, INV, MODE, false>;
+  static int blocks_per_sm[2] = {0, 0};
+  if (blocks_per_sm[w] == 0) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM) != cudaSuccess)
       return PM_ECUDA;
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, SH::THREADS, SH::SMEM);
-    blocks_per_sm = b > 0 ? b : 1;
+    blocks_per_sm[w] = b > 0 ? b : 1;
   }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int ntz = (M / 2 + 1 + TK - 1) / TK;
   const int ntiles = M * ntz;
-  int grid = sms * blocks_per_sm;
+  int grid = sms * blocks_per_sm[w];
   if (grid > ntiles) grid = ntiles;
   const int drop = c->inject == PM_INJECT_DROP_COPY ? 1 : 0;
   c->inject = 0;  // one shot

@@ -324,7 +324,8 @@ __device__ __forceinline__ float id_mass(const MassTable& mt, uint32_t id, int s
     *bad = true;
     return 0.0f;
   }
-  int shell = (int)((j / mt.ndir) % mt.nshell);
+  // 32-bit division: ids are below 2^32 (n_max < 2^32 - 1)
+  const int shell = (int)(((uint32_t)j / (uint32_t)mt.ndir) % (uint32_t)mt.nshell);
   return (species & PM_SPECIES_NU) ? mt.m_nu[shell] : 0.0f;
 }
 
