@@ -318,19 +318,40 @@ __device__ __forceinline__ void drift_next(const DriftNext& dn, const float (&F)
   const uint32_t kn = tile_key(uu[0], uu[1], uu[2], shift, ntl);
   const uint32_t ko = tile_key(ux, uy, uz, shift, ntl);
   dn.keys[i] = kn;
-  // counts: all particles by new key, stayers by new key, movers by old key, movers from
-  // a lower key by new key (warp-aggregated over the lanes here together)
+  // counts: all particles by new key, stayers by new key, movers by old key, movers from a
+  // lower key by new key.  The lanes here hold consecutive particles of the tile's sorted
+  // range, so their old keys never decrease from lane to lane: stayers (new key = old key)
+  // and movers are counted per run of equal old keys with ballots, and only the movers'
+  // new keys need a match over the lanes.
   const unsigned act = __activemask();
   const int lane = threadIdx.x & 31;
-  unsigned peers = __match_any_sync(act, kn);
-  if (lane == __ffs(peers) - 1) atomicAdd(dn.cnt3 + kn, (uint32_t)__popc(peers));
-  const uint32_t cat = kn == ko ? kn << 1 : (ko < kn ? (kn << 1) | 1u : 0xffffffffu);
-  peers = __match_any_sync(act, cat);
-  if (cat != 0xffffffffu && lane == __ffs(peers) - 1)
-    atomicAdd((cat & 1u) ? dn.low + (cat >> 1) : dn.cnt3 + dn.nb1 + (cat >> 1), (uint32_t)__popc(peers));
-  const uint32_t mo = kn != ko ? ko : 0xffffffffu;
-  peers = __match_any_sync(act, mo);
-  if (mo != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(dn.cnt3 + 2 * dn.nb1 + mo, (uint32_t)__popc(peers));
+  const bool stay = kn == ko;
+  const unsigned below = act & ((1u << lane) - 1u);
+  const int prev = below ? 31 - __clz(below) : lane;  // the nearest active lane below
+  const uint32_t ko_prev = __shfl_sync(act, ko, prev);
+  const bool head = prev == lane || ko_prev != ko;
+  const unsigned heads = __ballot_sync(act, head);
+  const unsigned stays = __ballot_sync(act, stay);
+  const unsigned lows = __ballot_sync(act, !stay && ko < kn);
+  if (head) {
+    const unsigned after = heads & ~((2u << lane) - 1u);  // heads above this lane (lane 31: none)
+    const unsigned upto = after ? (1u << (__ffs(after) - 1)) - 1u : 0xffffffffu;
+    const unsigned run = act & upto & ~((1u << lane) - 1u);
+    const uint32_t ns = (uint32_t)__popc(run & stays), nmv = (uint32_t)__popc(run & ~stays);
+    if (ns) {
+      atomicAdd(dn.cnt3 + ko, ns);
+      atomicAdd(dn.cnt3 + dn.nb1 + ko, ns);
+    }
+    if (nmv) atomicAdd(dn.cnt3 + 2 * dn.nb1 + ko, nmv);
+  }
+  if (!stay) {
+    const unsigned peers = __match_any_sync(act & ~stays, kn);
+    if (lane == __ffs(peers) - 1) {
+      atomicAdd(dn.cnt3 + kn, (uint32_t)__popc(peers));
+      const uint32_t nl = (uint32_t)__popc(peers & lows);
+      if (nl) atomicAdd(dn.low + kn, nl);
+    }
+  }
 }
 
 constexpr int kFd4Threads = 256;
