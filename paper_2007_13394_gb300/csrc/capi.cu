@@ -142,6 +142,7 @@ void free_all(pm_ctx* c) {
   ctx_free(c, c->hs_id);
   ctx_free(c, c->hs_f);
   ctx_free(c, c->adj);
+  ctx_free(c, c->paint_redo);
   mlp_free(c);
   for (auto& p : c->prof_live) {
     cudaEventDestroy(p.a);
@@ -490,7 +491,8 @@ int pm_init(const pm_config* cfg, pm_ctx** out) {
       dalloc(c, &c->rs_k2, nm) || dalloc(c, &c->rs_v2, nm) || dalloc(c, &c->rs_dev, 1) ||
       dalloc(c, &c->hist, 512 * hb) || dalloc(c, &c->hist_scan, 512 * hb) ||
       dalloc(c, &c->scan_tmp, c->scan_tmp_elems) || dalloc(c, &c->pk_partial, (size_t)N * 3 * 2048) ||
-      dalloc(c, &c->pk_final, 3 * 2048) || dalloc(c, &c->err_dev, 1)) {
+      dalloc(c, &c->pk_final, 3 * 2048) || dalloc(c, &c->err_dev, 1) ||
+      dalloc(c, &c->paint_redo, (size_t)c->nt * c->nt * c->nt + 1)) {
     free_all(c);
     delete c;
     return PM_ENOMEM;
@@ -974,7 +976,7 @@ const char* pm_kernel_name(int32_t k) {
       "fft_z_c2r",     "fft_x_plain",  "readout_kick", "kick_drift_keys", "power_bin",
       "power_reduce",  "ic_za",        "ic_assemble",  "repack",          "fft_x_fused",
       "readout3_kick", "adjoint",      "mlp_table",    "mlp_backward", "mlp_misc",
-      "fft_x_potential", "readout_fd4_kick", "resort_place", "resort_misc"};
+      "fft_x_potential", "readout_fd4_kick", "resort_place", "resort_misc", "paint_redo"};
   if (k < 0 || k >= K_NUM_KINDS) return "unknown";
   return names[k];
 }

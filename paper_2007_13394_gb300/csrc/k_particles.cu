@@ -47,20 +47,31 @@ __constant__ int8_t c_runs[14][3] = {{0, 0, 8}, {4, 4, 8}, {2, 2, 4}, {2, 6, 8},
 constexpr int kSy = 18, kSx = 292;
 constexpr int kAccWords = kTile * kSx;
 
-__global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
+// Paint of one tile.  FAST: 32-bit accumulators only (half the shared memory of the carry
+// form: zeroed, and read at the write-out, once per cell); a low word that wraps past 2^32
+// (a cell above 256 mean cell masses) cannot be resolved here, so the tile is written to
+// the redo list and left unwritten, and the redo pass paints it in full with the carry (or
+// 64-bit) form: the same exact integer sums, so the same floats.  Returns nothing; FAST
+// tiles with a wrap return before the write-out.
+template <bool FAST>
+__device__ __forceinline__ void paint_tile(
+    uint32_t tile, unsigned int* __restrict__ accw, uint32_t* __restrict__ run_lo, uint32_t* __restrict__ run_pre,
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
-    const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
-    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts,
-    float mmax) {
-  // one 64-bit accumulator, or the same bytes as two 32-bit halves (hi words, then lo words)
-  __shared__ long long acc[kAccWords];
-  unsigned int* const acc_hi = reinterpret_cast<unsigned int*>(acc);
-  unsigned int* const acc_lo = acc_hi + kAccWords;
-  __shared__ uint32_t run_lo[14], run_pre[15];
+    const uint32_t* __restrict__ bstart, float* __restrict__ mesh, const MassTable& mt, int species, int nm,
+    int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts, float mmax,
+    uint32_t* __restrict__ redo) {
+  // FAST: acc_lo only.  Else one 64-bit accumulator, or the same bytes as two 32-bit halves
+  // (hi words, then lo words) in the carry form.
+  long long* const acc = reinterpret_cast<long long*>(accw);
+  unsigned int* const acc_hi = accw;
+  unsigned int* const acc_lo = FAST ? accw : accw + kAccWords;
   const int t = threadIdx.x;
-  for (int i = t; i < kAccWords; i += kPaintThreads) acc[i] = 0;
+  if constexpr (FAST) {
+    for (int i = t; i < kAccWords / 4; i += kPaintThreads) reinterpret_cast<uint4*>(accw)[i] = make_uint4(0, 0, 0, 0);
+  } else {
+    for (int i = t; i < kAccWords; i += kPaintThreads) acc[i] = 0;
+  }
   const int nt = 1 << ntl;
-  const uint32_t tile = blockIdx.x;
   const int tx = tile >> (2 * ntl), ty = (tile >> ntl) & (nt - 1), tz = tile & (nt - 1);
   if (t < 32) {  // one warp resolves the 14 runs and their prefix
     uint32_t lo = 0, len = 0;
@@ -92,10 +103,10 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
   // the same thread.
   // carry form: 32-bit accumulators and conversions (GB300's FP64 pipe, which runs the
   // 64-bit float <-> integer conversions, is narrow); w 2^24 < 2^31 needs mmax < 128
-  const bool carry = wts == nullptr && mmax < 128.0f;
+  const bool carry = FAST || (wts == nullptr && mmax < 128.0f);
   const float fix = wts ? kFixW : kFixM;
   const int ox = tx * kTile, oy = ty * kTile, oz = tz * kTile;
-  bool bad = false;
+  bool bad = false, wrap = false;
   int r = 0;
   // the particle of iteration v + kPaintThreads is loaded while v's corners are added
   auto locate = [&](uint32_t v) {
@@ -147,7 +158,12 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
         if (carry) {
           const unsigned int q = __float2uint_rn(w * fix);  // < 2^31: masses below 128
           const unsigned int old = atomicAdd(&acc_lo[ad], q);
-          if (old + q < old) atomicAdd(&acc_hi[ad], 1u);  // the low word wrapped
+          if (old + q < old) {  // the low word wrapped
+            if constexpr (FAST)
+              wrap = true;
+            else
+              atomicAdd(&acc_hi[ad], 1u);
+          }
         } else {
           const long long q = __float2ll_rn(w * fix);
           atomicAdd((unsigned long long*)&acc[ad], (unsigned long long)q);
@@ -156,7 +172,16 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     }
   }
   if (bad) atomicOr(err, 1);
-  __syncthreads();
+  if constexpr (FAST) {
+    // the barrier's vote tells every thread whether any word wrapped (the redo pass then
+    // paints this tile)
+    if (__syncthreads_or(wrap ? 1 : 0)) {
+      if (t == 0) redo[1 + atomicAdd(redo, 1u)] = tile;
+      return;
+    }
+  } else {
+    __syncthreads();
+  }
   // write the tile: 256 rows of 16 floats, as float4
   for (int q = t; q < kTile * kTile * kTile / 4; q += kPaintThreads) {
     int row = q >> 2, z4 = (q & 3) * 4;
@@ -165,7 +190,9 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     float fv[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      if (carry) {
+      if constexpr (FAST) {
+        fv[e] = __uint2float_rn(acc_lo[a0 + e]);
+      } else if (carry) {
         // value = carry 2^32 + low word: without a carry the correctly rounded 32-bit
         // conversion is that of the 64-bit sum
         const unsigned int hi = acc_hi[a0 + e], lo = acc_lo[a0 + e];
@@ -179,6 +206,37 @@ __global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
     float4 v = make_float4(fv[0] * un, fv[1] * un, fv[2] * un, fv[3] * un);
     size_t off = ((size_t)(ox + lx) * nm + (oy + ly)) * (size_t)row_pitch + oz + z4;
     *reinterpret_cast<float4*>(mesh + off) = v;
+  }
+}
+
+// One CTA per tile.  FAST: the 32-bit form with wrapped tiles sent to the redo list
+// (redo[0] = count, redo[1 ..] = tiles); else the carry or 64-bit form.
+template <bool FAST>
+__global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
+    const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
+    const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
+    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts,
+    float mmax, uint32_t* __restrict__ redo) {
+  __shared__ __align__(16) unsigned int accw[FAST ? kAccWords : 2 * kAccWords];
+  __shared__ uint32_t run_lo[14], run_pre[15];
+  paint_tile<FAST>(blockIdx.x, accw, run_lo, run_pre, us, ids, n, bstart, mesh, mt, species, nm, shift, ntl,
+                   row_pitch, err, wts, mmax, redo);
+}
+
+// The redo pass: the tiles the fast pass listed, painted with the carry form (persistent
+// CTAs walk the list; an empty list costs one launch).
+__global__ void __launch_bounds__(kPaintThreads) k_paint_redo(
+    const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
+    const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
+    int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, float mmax,
+    const uint32_t* __restrict__ redo) {
+  __shared__ __align__(16) unsigned int accw[2 * kAccWords];
+  __shared__ uint32_t run_lo[14], run_pre[15];
+  const uint32_t count = redo[0];
+  for (uint32_t q = blockIdx.x; q < count; q += gridDim.x) {
+    paint_tile<false>(redo[1 + q], accw, run_lo, run_pre, us, ids, n, bstart, mesh, mt, species, nm, shift, ntl,
+                      row_pitch, err, nullptr, mmax, nullptr);
+    __syncthreads();  // the shared accumulators are reused by the next tile
   }
 }
 
@@ -571,15 +629,32 @@ __global__ void k_repack_complex(const float2* __restrict__ src, int sp, float2*
 
 void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, int species,
                  float* mesh, int row_pitch, cudaStream_t s, const float* weights) {
-  LaunchScope L(c, s, K_PAINT);
   unsigned grid = (unsigned)(c->nt * c->nt * c->nt);
   float mmax = 0.0f;  // largest particle mass of the painted species
   if (species & PM_SPECIES_CDM) mmax = std::max(mmax, c->mt.m_cdm);
   if (species & PM_SPECIES_NU)
     for (int i = 0; i < c->mt.nshell && i < kMaxShell; ++i) mmax = std::max(mmax, c->mt.m_nu[i]);
-  k_paint_tiles<<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species,
-                                               c->g.n, 32 - c->g.logn, c->ntl, row_pitch,
-                                               c->err_dev, weights, mmax);
+  if (weights == nullptr && mmax < 128.0f && c->paint_redo) {
+    // 32-bit pass, then the tiles whose words wrapped, in the carry form
+    cudaMemsetAsync(c->paint_redo, 0, sizeof(uint32_t), s);
+    {
+      LaunchScope L(c, s, K_PAINT);
+      k_paint_tiles<true><<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species, c->g.n,
+                                                         32 - c->g.logn, c->ntl, row_pitch, c->err_dev, nullptr,
+                                                         mmax, c->paint_redo);
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    LaunchScope L(c, s, K_PAINT_REDO);
+    k_paint_redo<<<(unsigned)std::min<long long>(2LL * sms, grid), kPaintThreads, 0, s>>>(
+        us, ids, n, c->bstart, mesh, c->mt, species, c->g.n, 32 - c->g.logn, c->ntl, row_pitch, c->err_dev, mmax,
+        c->paint_redo);
+    return;
+  }
+  LaunchScope L(c, s, K_PAINT);
+  k_paint_tiles<false><<<grid, kPaintThreads, 0, s>>>(us, ids, n, c->bstart, mesh, c->mt, species, c->g.n,
+                                                      32 - c->g.logn, c->ntl, row_pitch, c->err_dev, weights, mmax,
+                                                      nullptr);
 }
 
 void readout_kick(pm_ctx* c, const uint32_t* us, const float* ps, const uint32_t* ids, int64_t n,

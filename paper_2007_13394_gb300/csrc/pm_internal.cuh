@@ -45,6 +45,7 @@ enum Kind {
   K_READOUT_FD4_KICK,
   K_RESORT_PLACE,
   K_RESORT_MISC,
+  K_PAINT_REDO,
   K_NUM_KINDS
 };
 
@@ -180,6 +181,8 @@ struct pm_ctx {
   // device memory held, by allocation, against cfg.mem_limit
   std::unordered_map<void*, size_t> allocs;
   size_t mem_used = 0;
+  // the paint's redo list: count, then the tiles whose 32-bit accumulators wrapped
+  uint32_t* paint_redo = nullptr;
   // pending test injection (pm_test_inject), consumed by the launch it targets
   int inject = 0;
   // instrumentation

@@ -168,6 +168,29 @@ def test_paint_clustered_tiles(pm):
     np.testing.assert_allclose(m, ref, rtol=2e-6, atol=2e-6 * ref.max())
 
 
+@pytest.mark.parametrize("cell", [(80, 48, 48), (79, 47, 47), (5, 6, 7)], ids=["tile_origin", "tile_corner", "interior"])
+def test_paint_dense_cells_that_wrap_32_bit_words(pm, cell):
+    """Cells above 256 mean cell masses wrap the paint's 32-bit fixed-point words: such tiles
+    are repainted whole in the carry form.  A cell with 100 (no wrap), 300 and 1000 particles
+    (one to four wraps in each of the 8 cells around it), at a tile's origin, at a tile's far
+    corner (its 8 CIC cells in 8 tiles) and inside a tile: the whole mesh against the
+    oracle, on meshes reused between calls (a tile left unwritten would show stale values)."""
+    cfg = make_cfg(pm, nmesh=256, nc=128, nsites=0, box=256.0, m_nu=(0.0, 0.0, 0.0), n_max=4000)
+    ctx = pm.ParticleMesh(cfg)
+    bg = obg.Background.physical(cfg.h, cfg.omega_m, nu_masses_ev=cfg.m_nu)
+    mc, _ = onu.species_masses(256, 128, 0, cfg.nshell, cfg.nfib, bg.omega_c, bg.omega_nu_poisson, np.zeros(0))
+    rng = np.random.default_rng(sum(cell))
+    for count in (100, 300, 1000, 300):
+        u = np.empty((3, count), np.uint32)
+        for d in range(3):
+            u[d] = (cell[d] * (2 ** 32 // 256) + rng.integers(0, 2 ** 32 // 256, count)).astype(np.uint32)
+        m = ctx.paint(pm.as_u32_tensor(u)).cpu().numpy()
+        ctx.sync()
+        ref = opm.paint(u, np.full(count, mc), 256)
+        assert ref.max() > 256 or count == 100
+        np.testing.assert_allclose(m, ref, rtol=2e-6, atol=2e-6 * ref.max())
+
+
 def test_paint_rejects_unknown_ids(pm):
     cfg = make_cfg(pm)
     ctx = pm.ParticleMesh(cfg)
