@@ -46,13 +46,31 @@ __constant__ int8_t c_runs[14][3] = {{0, 0, 8}, {4, 4, 8}, {2, 2, 4}, {2, 6, 8},
 // 8 distinct 8-byte bank pairs.
 constexpr int kSy = 18, kSx = 292;
 constexpr int kAccWords = kTile * kSx;
+// fast paint: wrap bitmap words, event list capacity, and the whole shared area in words
+// (low words, bitmap, event count, 16-bit events, rounded up to whole 16-byte groups)
+constexpr int kWrapBits = (kAccWords + 31) / 32;
+constexpr unsigned int kWraps = 1024;
+constexpr int kFastWords = ((kAccWords + kWrapBits + 1 + kWraps / 2) + 3) / 4 * 4;
 
-// Paint of one tile.  FAST: 32-bit accumulators only (half the shared memory of the carry
-// form: zeroed, and read at the write-out, once per cell); a low word that wraps past 2^32
-// (a cell above 256 mean cell masses) cannot be resolved here, so the tile is written to
-// the redo list and left unwritten, and the redo pass paints it in full with the carry (or
-// 64-bit) form: the same exact integer sums, so the same floats.  Returns nothing; FAST
-// tiles with a wrap return before the write-out.
+// Records that the fast paint's low word ad wrapped: its bit in the bitmap and an event in
+// the list (layout of paint_tile); false when the list is full.  Out of line: rarely taken,
+// and it keeps the paint's inner loop at fewer registers.
+__device__ __noinline__ bool record_wrap(unsigned int* accw, unsigned int ad) {
+  atomicOr(accw + kAccWords + (ad >> 5), 1u << (ad & 31));
+  const unsigned int e = atomicAdd(accw + kAccWords + kWrapBits, 1u);
+  if (e >= kWraps) return false;
+  reinterpret_cast<unsigned short*>(accw + kAccWords + kWrapBits + 1)[e] = (unsigned short)ad;
+  return true;
+}
+
+// Paint of one tile.  FAST: 32-bit low words only (half the shared memory of the carry form:
+// zeroed, and read at the write-out, once per cell).  A low word that wraps past 2^32 (the
+// cell passes another 256 mean cell masses) is recorded as an event -- the cell's bit in a
+// bitmap, its index in a list of up to kWraps events -- and at the write-out a cell whose
+// bit is set counts its events in the list: value = events 2^32 + low word.  A tile with
+// more events than the list holds is written to the redo list and left unwritten; the redo
+// pass paints it in full with the 32-bit carry (or 64-bit) form.  Every form sums the same
+// exact integers, so all give the same floats.
 template <bool FAST>
 __device__ __forceinline__ void paint_tile(
     uint32_t tile, unsigned int* __restrict__ accw, uint32_t* __restrict__ run_lo, uint32_t* __restrict__ run_pre,
@@ -60,14 +78,19 @@ __device__ __forceinline__ void paint_tile(
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, const MassTable& mt, int species, int nm,
     int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts, float mmax,
     uint32_t* __restrict__ redo) {
-  // FAST: acc_lo only.  Else one 64-bit accumulator, or the same bytes as two 32-bit halves
-  // (hi words, then lo words) in the carry form.
+  // FAST: low words, then the wrap bitmap, the event count and the event list.  Else one
+  // 64-bit accumulator, or the same bytes as two 32-bit halves (hi words, then lo words) in the
+  // carry form.
   long long* const acc = reinterpret_cast<long long*>(accw);
   unsigned int* const acc_hi = accw;
   unsigned int* const acc_lo = FAST ? accw : accw + kAccWords;
+  volatile unsigned int* const wbits = accw + kAccWords;          // FAST: kWrapBits words
+  unsigned int* const wcount = accw + kAccWords + kWrapBits;       // FAST: one word
+  volatile unsigned short* const wlist = reinterpret_cast<unsigned short*>(accw + kAccWords + kWrapBits + 1);
   const int t = threadIdx.x;
   if constexpr (FAST) {
-    for (int i = t; i < kAccWords / 4; i += kPaintThreads) reinterpret_cast<uint4*>(accw)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = t; i < (kAccWords + kWrapBits + 1) / 4 + 1; i += kPaintThreads)
+      reinterpret_cast<uint4*>(accw)[i] = make_uint4(0, 0, 0, 0);
   } else {
     for (int i = t; i < kAccWords; i += kPaintThreads) acc[i] = 0;
   }
@@ -159,10 +182,11 @@ __device__ __forceinline__ void paint_tile(
           const unsigned int q = __float2uint_rn(w * fix);  // < 2^31: masses below 128
           const unsigned int old = atomicAdd(&acc_lo[ad], q);
           if (old + q < old) {  // the low word wrapped
-            if constexpr (FAST)
-              wrap = true;
-            else
+            if constexpr (FAST) {
+              if (!record_wrap(accw, ad)) wrap = true;  // the list is full: the tile is repainted
+            } else {
               atomicAdd(&acc_hi[ad], 1u);
+            }
           }
         } else {
           const long long q = __float2ll_rn(w * fix);
@@ -173,8 +197,8 @@ __device__ __forceinline__ void paint_tile(
   }
   if (bad) atomicOr(err, 1);
   if constexpr (FAST) {
-    // the barrier's vote tells every thread whether any word wrapped (the redo pass then
-    // paints this tile)
+    // the barrier's vote tells every thread whether the event list overflowed (the redo pass
+    // then paints this tile)
     if (__syncthreads_or(wrap ? 1 : 0)) {
       if (t == 0) redo[1 + atomicAdd(redo, 1u)] = tile;
       return;
@@ -182,6 +206,9 @@ __device__ __forceinline__ void paint_tile(
   } else {
     __syncthreads();
   }
+  // FAST: whether any low word of the tile wrapped (else the write-out reads low words only)
+  bool any_wrap = false;
+  if constexpr (FAST) any_wrap = *(volatile unsigned int*)wcount != 0u;
   // write the tile: 256 rows of 16 floats, as float4
   for (int q = t; q < kTile * kTile * kTile / 4; q += kPaintThreads) {
     int row = q >> 2, z4 = (q & 3) * 4;
@@ -191,7 +218,15 @@ __device__ __forceinline__ void paint_tile(
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if constexpr (FAST) {
-        fv[e] = __uint2float_rn(acc_lo[a0 + e]);
+        const unsigned int ad = a0 + e, lo = acc_lo[ad];
+        if (any_wrap && ((wbits[ad >> 5] >> (ad & 31)) & 1u)) {  // the cell wrapped: count its events
+          const unsigned int ne = *(volatile unsigned int*)wcount;
+          unsigned int hi = 0;
+          for (unsigned int k = 0; k < ne; ++k) hi += wlist[k] == ad ? 1u : 0u;
+          fv[e] = __ull2float_rn(((unsigned long long)hi << 32) + (unsigned long long)lo);
+        } else {
+          fv[e] = __uint2float_rn(lo);
+        }
       } else if (carry) {
         // value = carry 2^32 + low word: without a carry the correctly rounded 32-bit
         // conversion is that of the 64-bit sum
@@ -209,22 +244,23 @@ __device__ __forceinline__ void paint_tile(
   }
 }
 
-// One CTA per tile.  FAST: the 32-bit form with wrapped tiles sent to the redo list
-// (redo[0] = count, redo[1 ..] = tiles); else the carry or 64-bit form.
+// One CTA per tile.  FAST: the 32-bit form with wrap events, tiles whose event list
+// overflows sent to the redo list (redo[0] = count, redo[1 ..] = tiles); else the carry or
+// 64-bit form.
 template <bool FAST>
-__global__ void __launch_bounds__(kPaintThreads) k_paint_tiles(
+__global__ void __launch_bounds__(kPaintThreads, FAST ? 8 : 1) k_paint_tiles(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
     int nm, int shift, int ntl, int row_pitch, int* __restrict__ err, const float* __restrict__ wts,
     float mmax, uint32_t* __restrict__ redo) {
-  __shared__ __align__(16) unsigned int accw[FAST ? kAccWords : 2 * kAccWords];
+  __shared__ __align__(16) unsigned int accw[FAST ? kFastWords : 2 * kAccWords];
   __shared__ uint32_t run_lo[14], run_pre[15];
   paint_tile<FAST>(blockIdx.x, accw, run_lo, run_pre, us, ids, n, bstart, mesh, mt, species, nm, shift, ntl,
                    row_pitch, err, wts, mmax, redo);
 }
 
-// The redo pass: the tiles the fast pass listed, painted with the carry form (persistent
-// CTAs walk the list; an empty list costs one launch).
+// The redo pass: the tiles the fast pass listed, painted with the 32-bit carry form
+// (persistent CTAs walk the list; an empty list, the normal case, costs one launch).
 __global__ void __launch_bounds__(kPaintThreads) k_paint_redo(
     const uint32_t* __restrict__ us, const uint32_t* __restrict__ ids, int64_t n,
     const uint32_t* __restrict__ bstart, float* __restrict__ mesh, MassTable mt, int species,
@@ -643,10 +679,15 @@ void paint_tiles(pm_ctx* c, const uint32_t* us, const uint32_t* ids, int64_t n, 
                                                          32 - c->g.logn, c->ntl, row_pitch, c->err_dev, nullptr,
                                                          mmax, c->paint_redo);
     }
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    // persistent CTAs, as many as fit: the list is short, or empty, in most steps
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_paint_redo, kPaintThreads, 0);
+      if (per_sm < 1) per_sm = 1;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    }
     LaunchScope L(c, s, K_PAINT_REDO);
-    k_paint_redo<<<(unsigned)std::min<long long>(2LL * sms, grid), kPaintThreads, 0, s>>>(
+    k_paint_redo<<<(unsigned)std::min<long long>((long long)per_sm * sms, grid), kPaintThreads, 0, s>>>(
         us, ids, n, c->bstart, mesh, c->mt, species, c->g.n, 32 - c->g.logn, c->ntl, row_pitch, c->err_dev, mmax,
         c->paint_redo);
     return;
