@@ -281,7 +281,9 @@ __device__ __forceinline__ void copy_particle(const uint32_t* __restrict__ u, co
 }
 
 // One CTA per old tile O: walks O's range [bprev[8 O], bprev[8 O + 8]) in chunks of the
-// block size, in index order.  A block scan of the mover flags gives every particle the
+// block size, in index order.  With stage, a mover's position, momentum and id also go to a
+// 32-byte record at its list position (the placement then reads one sector a mover
+// instead of seven scattered words), and mv holds that position.  A block scan of the mover flags gives every particle the
 // number of movers of its own old key before it (mrank); a stayer goes to
 // bstart[B] + low[B] + (i - bprev[B]) - mrank, a mover's (new key, index) to its old
 // key's slot of the mover list, mstart3[ko] - base3 + mrank (movers in index order).
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kResortThreads) k_resort_old_tiles(
     const uint32_t* __restrict__ keys, const uint32_t* __restrict__ bprev, const uint32_t* __restrict__ bstart3,
     long long nb1, const uint32_t* __restrict__ low, uint32_t* __restrict__ us, float* __restrict__ ps,
     uint32_t* __restrict__ ids, uint32_t* __restrict__ mk, uint32_t* __restrict__ mv, int64_t nm,
-    int* __restrict__ err) {
+    int* __restrict__ err, uint4* __restrict__ stage) {
   constexpr int W = kResortThreads / 32;
   __shared__ uint32_t cls_lo[9];   // bprev[8 O + c]
   __shared__ uint32_t cls_m0[8];   // movers of the tile before class c's first particle
@@ -357,7 +359,14 @@ __global__ void __launch_bounds__(kResortThreads) k_resort_old_tiles(
         const uint32_t pos = run0 + mrank;
         if (pos < (uint64_t)nm) {
           mk[pos] = kn;
-          mv[pos] = i;
+          if (stage) {  // the mover's 28 bytes as one 32-byte record at its list position
+            mv[pos] = pos;
+            stage[2 * (size_t)pos] = make_uint4(pu[0], pu[1], pu[2], pid);
+            stage[2 * (size_t)pos + 1] = make_uint4(__float_as_uint(pp[0]), __float_as_uint(pp[1]),
+                                                    __float_as_uint(pp[2]), 0u);
+          } else {
+            mv[pos] = i;
+          }
         } else {
           atomicOr(err, 1);
         }
@@ -377,21 +386,35 @@ __global__ void k_place_movers(const uint32_t* __restrict__ mk, const uint32_t* 
                                const uint32_t* __restrict__ id, int64_t n, const uint32_t* __restrict__ bstart3,
                                long long nb1, long long nbuckets, const uint32_t* __restrict__ low,
                                uint32_t* __restrict__ us, float* __restrict__ ps, uint32_t* __restrict__ ids,
-                               int* __restrict__ err) {
+                               int* __restrict__ err, const uint4* __restrict__ stage) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nm) return;
   const uint32_t B = mk[j];
-  if (B >= (uint64_t)nbuckets || mv[j] >= (uint64_t)n) {
+  if (B >= (uint64_t)nbuckets || mv[j] >= (uint64_t)(stage ? nm : n)) {
     atomicOr(err, 1);
     return;
   }
   const uint32_t s0 = bstart3[nb1 + B], s1 = bstart3[nb1 + B + 1];
   const uint32_t r = (uint32_t)j - (bstart3[B] - (s0 - (uint32_t)n));
   const uint32_t dst = bstart3[B] + r + (r >= low[B] ? s1 - s0 : 0u);
-  if (dst < (uint64_t)n)
-    copy_particle(u, p, id, n, mv[j], dst, us, ps, ids);
-  else
+  if (dst >= (uint64_t)n) {
     atomicOr(err, 1);
+    return;
+  }
+  if (stage) {  // one 32-byte record (mv: its position in the mover list)
+    const uint4 a = stage[2 * (size_t)mv[j]], b = stage[2 * (size_t)mv[j] + 1];
+    us[dst] = a.x;
+    us[n + dst] = a.y;
+    us[2 * n + dst] = a.z;
+    ids[dst] = a.w;
+    if (p) {
+      ps[dst] = __uint_as_float(b.x);
+      ps[n + dst] = __uint_as_float(b.y);
+      ps[2 * n + dst] = __uint_as_float(b.z);
+    }
+  } else {
+    copy_particle(u, p, id, n, mv[j], dst, us, ps, ids);
+  }
 }
 
 }  // namespace
@@ -520,11 +543,15 @@ int resort_near_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint3
   const int64_t nm = (int64_t)c->rs_host[2] - (int64_t)c->rs_host[1];
   if (nm < 0 || nm > n || (nm + kRadixTile - 1) / kRadixTile > c->hist_blocks_max) return PM_EINVAL;
   c->rs_last_movers = nm;
+  // the movers' records go to the second mesh, free during a step, when they fit (32 bytes a
+  // mover: up to 2^30 movers at 2048^3); else the placement gathers from the state itself
+  uint4* stage = nullptr;
+  if (c->meshB && (size_t)nm * 32 <= c->g.elems() * sizeof(float2)) stage = reinterpret_cast<uint4*>(c->meshB);
   {
     LaunchScope L(c, s, K_RESORT_PLACE);
     k_resort_old_tiles<<<(unsigned)((long long)c->nt * c->nt * c->nt), kResortThreads, 0, s>>>(
         u, p, id, n, c->keys[0], c->bprev, c->bstart, nb1, c->rs_low, c->us, c->ps, c->ids, c->keys[1], c->vals[1],
-        nm, c->err_dev);
+        nm, c->err_dev, stage);
   }
   if (nm > 0) {
     uint32_t* const kb[2] = {c->keys[1], c->rs_k2};
@@ -533,7 +560,7 @@ int resort_near_sorted(pm_ctx* c, const uint32_t* u, const float* p, const uint3
     LaunchScope L(c, s, K_RESORT_MISC);
     k_place_movers<<<(unsigned)((nm + 255) / 256), 256, 0, s>>>(kb[r], vb[r], nm, u, p, id, n, c->bstart, nb1,
                                                                  c->nbuckets, c->rs_low, c->us, c->ps, c->ids,
-                                                                 c->err_dev);
+                                                                 c->err_dev, stage);
   }
   return 1;
 }
