@@ -1,10 +1,10 @@
 // Stockham FFT engine shared by the FFT kernels (device code only).
 //
 // A line of M points (M a power of two, 16 <= M <= 2048) is held by M/V threads,
-// V = 16 (or 8) values each (value s of thread j is element j + s M/V).  Stockham
+// V = 16 (8 or 32) values each (value s of thread j is element j + s M/V).  Stockham
 // stages of radix V (the last stage radix 2..V) run in registers; between stages the line
-// goes through shared memory, padded by one float2 per 16 so that the stride-16
-// writes of the first stage are free of bank conflicts.  A line's elements may be
+// goes through shared memory, padded by one float2 per 16 (per 32 when V = 32) so that
+// the stride-V writes of the first stage are free of bank conflicts.  A line's elements may be
 // interleaved with other lines' (column stride cs in shared memory).  Twiddles
 // come from a table e^{-2 pi i t / TWN} computed in double precision on the host.
 #pragma once
@@ -15,6 +15,12 @@ namespace pmnu {
 namespace fft {
 
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+
+// shared-memory index of element i of a line held V values a thread
+template <int V>
+__device__ __forceinline__ int padv(int i) {
+  return V >= 32 ? i + (i >> 5) : padi(i);
+}
 
 // e^{s 2 pi i m / 16} for compile-time m, s = -1 forward, +1 inverse
 template <int m, bool INV>
@@ -43,6 +49,33 @@ __device__ __forceinline__ float2 rot16(float2 a) {
   }
 }
 
+// e^{s 2 pi i m / 32} for odd compile-time m (the last layer of a 32-point DFT)
+template <int m, bool INV>
+__device__ __forceinline__ float2 w32() {
+  // cos(2 pi t / 32), t = 0 .. 8
+  constexpr float C[9] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                          0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                          0.19509032201612826785f, 0.0f};
+  constexpr int t = m & 31;  // cos and sin of 2 pi t / 32 from the first quadrant
+  constexpr int q = t & 7, qq = t >> 3;
+  constexpr float c0 = C[q], s0 = C[8 - q];
+  constexpr float cv = qq == 0 ? c0 : qq == 1 ? -s0 : qq == 2 ? -c0 : s0;
+  constexpr float sv = qq == 0 ? s0 : qq == 1 ? c0 : qq == 2 ? -s0 : -c0;
+  return INV ? make_float2(cv, sv) : make_float2(cv, -sv);
+}
+
+// rotation by e^{s 2 pi i K / LEN} in a radix-2 layer of length LEN <= 32
+template <int K, int LEN, bool INV>
+__device__ __forceinline__ float2 rotl(float2 a) {
+  if constexpr (LEN <= 16) {
+    return rot16<K * (16 / LEN), INV>(a);
+  } else if constexpr ((K & 1) == 0) {
+    return rot16<K / 2, INV>(a);
+  } else {
+    return cmul(a, w32<K, INV>());
+  }
+}
+
 template <int R>
 __host__ __device__ constexpr int brev(int i) {
   int r = 0;
@@ -51,7 +84,7 @@ __host__ __device__ constexpr int brev(int i) {
   return r;
 }
 
-// In-register DFT of size R (2, 4, 8, 16): radix-2 decimation in time.
+// In-register DFT of size R (2, 4, 8, 16, 32): radix-2 decimation in time.
 template <int R, bool INV, int LEN = 2>
 __device__ __forceinline__ void dft_layers(float2 (&x)[R]);
 
@@ -60,7 +93,7 @@ __device__ __forceinline__ void dft_bfly(float2 (&x)[R]) {
   if constexpr (I < R) {
     if constexpr (K < LEN / 2) {
       float2 a = x[I + K];
-      float2 b = rot16<K * (16 / LEN), INV>(x[I + K + LEN / 2]);
+      float2 b = rotl<K, LEN, INV>(x[I + K + LEN / 2]);
       x[I + K] = cadd(a, b);
       x[I + K + LEN / 2] = csub(a, b);
       dft_bfly<R, INV, LEN, I, K + 1>(x);
@@ -136,13 +169,13 @@ __device__ __forceinline__ void stage(float2 (&v)[V], int j, float2* sm, int cs,
     } else {
       const int base = (jj / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
+      for (int r = 0; r < R; ++r) sm[padv<V>(base + r * NS) * cs] = x[r];
     }
   }
   if constexpr (!LAST) {
     line_sync<WARP>();
 #pragma unroll
-    for (int s = 0; s < V; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    for (int s = 0; s < V; ++s) v[s] = sm[padv<V>(j + s * Q) * cs];
     line_sync<WARP>();
   }
 }
@@ -217,13 +250,13 @@ __device__ __forceinline__ void stage_reg(float2 (&v)[V], int j, float2* sm, int
     } else {
       const int base = (jj / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[padi(base + r * NS) * cs] = x[r];
+      for (int r = 0; r < R; ++r) sm[padv<V>(base + r * NS) * cs] = x[r];
     }
   }
   if constexpr (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < V; ++s) v[s] = sm[padi(j + s * Q) * cs];
+    for (int s = 0; s < V; ++s) v[s] = sm[padv<V>(j + s * Q) * cs];
     __syncthreads();
   }
 }
@@ -249,24 +282,25 @@ __device__ __forceinline__ float2 gload(const float2* p) {
 }
 
 // z pass, real -> complex, of one row: N reals read as M = N/2 complex values, held by
-// M/16 threads (j = 0 .. M/16 - 1) with 16 values each; ls is the row's shared-memory line
-// (M + M/16 + 2 float2).  Writes the N/2 + 1 modes k = 0 .. M over the row in place.
-// ok = false: the thread takes part in the barriers only.
-template <int LOGN, bool WARP, bool CG>
+// M/V threads (j = 0 .. M/V - 1) with V values each (V = 16, or 32 for rows of 1024 and
+// 2048 points: one exchange through shared memory fewer); ls is the row's shared-memory
+// line (z_line<LOGN, V>() float2).  Writes the N/2 + 1 modes k = 0 .. M over the row in
+// place.  ok = false: the thread takes part in the barriers only.
+template <int LOGN, bool WARP, bool CG, int V = 16>
 __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16;
-  float2 v[16];
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / V;
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 16; ++s) v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
-  run_stages<M, N, 1, false, 16, WARP>(v, j, ls, 1, tw);
+  for (int s = 0; s < V; ++s) v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
+  run_stages<M, N, 1, false, V, WARP>(v, j, ls, 1, tw);
 #pragma unroll
-  for (int s = 0; s < 16; ++s) ls[padi(j + s * TPL)] = v[s];
+  for (int s = 0; s < V; ++s) ls[padv<V>(j + s * TPL)] = v[s];
   line_sync<WARP>();
   if (ok) {
     for (int k = j; k <= M; k += TPL) {
-      float2 zk = ls[padi(k & (M - 1))];
-      float2 zm = cconj(ls[padi((M - k) & (M - 1))]);
+      float2 zk = ls[padv<V>(k & (M - 1))];
+      float2 zm = cconj(ls[padv<V>((M - k) & (M - 1))]);
       float2 e = cscale(cadd(zk, zm), 0.5f);
       float2 o = cscale(csub(zk, zm), 0.5f);
       float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
@@ -277,23 +311,23 @@ __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int 
 }
 
 // z pass, complex -> real, of one row in place (the inverse of z_r2c_row, unnormalised).
-template <int LOGN, bool WARP, bool CG>
+template <int LOGN, bool WARP, bool CG, int V = 16>
 __device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16;
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / V;
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
+  for (int s = 0; s < V; ++s) {
     const int k = j + s * TPL;
-    ls[padi(k)] = ok ? gload<CG>(rp + k) : make_float2(0.f, 0.f);
+    ls[padv<V>(k)] = ok ? gload<CG>(rp + k) : make_float2(0.f, 0.f);
   }
-  if (j == 0) ls[padi(M)] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
+  if (j == 0) ls[padv<V>(M)] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
   line_sync<WARP>();
-  float2 v[16];
+  float2 v[V];
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
+  for (int s = 0; s < V; ++s) {
     const int k = j + s * TPL;
-    float2 xk = ls[padi(k)];
-    float2 xm = cconj(ls[padi(M - k)]);
+    float2 xk = ls[padv<V>(k)];
+    float2 xm = cconj(ls[padv<V>(M - k)]);
     float2 e = cadd(xk, xm);
     float2 d = csub(xk, xm);
     float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
@@ -301,11 +335,21 @@ __device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int 
     v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
   }
   line_sync<WARP>();
-  run_stages<M, N, 1, true, 16, WARP>(v, j, ls, 1, tw);
+  run_stages<M, N, 1, true, V, WARP>(v, j, ls, 1, tw);
   if (ok) {
 #pragma unroll
-    for (int s = 0; s < 16; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
+    for (int s = 0; s < V; ++s) rp[j + s * TPL] = v[s];  // (x[2n], x[2n+1])
   }
+}
+
+// values a thread and shared-memory line length (float2) of the z passes
+template <int LOGN>
+__host__ __device__ constexpr int z_values() {
+  return LOGN >= 10 ? 32 : 16;
+}
+template <int LOGN, int V = z_values<LOGN>()>
+__host__ __device__ constexpr int z_line() {
+  return (1 << (LOGN - 1)) + (1 << (LOGN - 1)) / (V >= 32 ? 32 : 16) + 2;
 }
 
 // Fused epilogue / prologue of the x pass.

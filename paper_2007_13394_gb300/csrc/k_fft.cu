@@ -10,13 +10,14 @@
 // one mesh: z r2c, y, x forward + Green's function + x inverse in one kernel, y
 // inverse, z c2r.
 //
-// Each line of M points is held by M/16 threads, 16 values each (value s of
-// thread j is element j + s M/16).  Stockham stages of radix 16 (the last stage
-// radix 2..16) run in registers; between stages the line goes through shared
-// memory, padded by one float2 per 16 to keep the stride-16 writes free of bank
-// conflicts.  The first stage reads global memory directly and the last stage
-// writes it directly, both coalesced.  Twiddles come from a table
-// e^{-2 pi i t / N} computed in double precision on the host.
+// Each line of M points is held by M/V threads, V = 16 values each (value s of thread
+// j is element j + s M/V); z rows of 1024 and 2048 points use V = 32, so that their
+// M = 512 and 1024 complex points take two stages instead of three.  Stockham stages of
+// radix V (the last stage radix 2..V) run in registers; between stages the line goes
+// through shared memory, padded by one float2 per 16 (per 32 when V = 32) to keep the
+// stride-V writes free of bank conflicts.  The first stage reads global memory directly and the last stage
+// writes it directly, both coalesced.  Twiddles come from a table e^{-2 pi i t / N}
+// computed in double precision on the host.
 //
 // The strided passes (y, x) put TK adjacent kz columns in one CTA, lane-fastest,
 // so each global access covers TK consecutive float2.
@@ -31,37 +32,42 @@ namespace {
 
 using namespace fft;
 
-// z-pass CTA size: 128 threads (two rows) from 2048-point rows up, so that more CTAs in
-// different load / transform / store phases share an SM; 256 below
+// z-pass CTA size: 128 threads from 1024-point rows up (rows held 32 values a thread,
+// four or eight rows a CTA, 128 registers a thread), so that more CTAs in different
+// load / transform / store phases share an SM; 256 below (16 values, 64 registers).
 template <int LOGN>
 constexpr int z_threads() {
-  return LOGN >= 11 ? 128 : 256;
+  return LOGN >= 10 ? 128 : 256;
+}
+template <int LOGN>
+constexpr int z_min_blocks() {
+  return (z_values<LOGN>() >= 32 ? 512 : 1024) / z_threads<LOGN>();
 }
 
 // z pass, real -> complex, in place on rows of pitch P float2.
 template <int LOGN, int NT = z_threads<LOGN>()>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
-                                                          int pc, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
-  constexpr int LS = M + M / 16 + 2;  // line stride in shared memory
+__global__ void __launch_bounds__(NT, z_min_blocks<LOGN>()) k_fft_z_r2c(float2* __restrict__ data, long long nrows,
+                                                                        int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, V = z_values<LOGN>(), TPL = M / V, LPC = NT / TPL;
+  constexpr int LS = z_line<LOGN>();  // line stride in shared memory
   constexpr bool WARP = TPL <= 32;    // a row's threads within one warp: warp barriers suffice
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  z_r2c_row<LOGN, WARP, false>(data + row * pc, row < nrows, j, sm + line * LS, tw);
+  z_r2c_row<LOGN, WARP, false, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 // z pass, complex -> real, in place.
 template <int LOGN, int NT = z_threads<LOGN>()>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
-                                                          int pc, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = NT / TPL;
-  constexpr int LS = M + M / 16 + 2;
+__global__ void __launch_bounds__(NT, z_min_blocks<LOGN>()) k_fft_z_c2r(float2* __restrict__ data, long long nrows,
+                                                                        int pc, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, M = N / 2, V = z_values<LOGN>(), TPL = M / V, LPC = NT / TPL;
+  constexpr int LS = z_line<LOGN>();
   constexpr bool WARP = TPL <= 32;  // a row's threads within one warp: warp barriers suffice
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  z_c2r_row<LOGN, WARP, false>(data + row * pc, row < nrows, j, sm + line * LS, tw);
+  z_c2r_row<LOGN, WARP, false, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 
@@ -230,8 +236,8 @@ void launch_strided(const float2* src, float2* dst, int axis, int pc, const floa
 template <int LOGN>
 void launch_z(float2* data, long long nrows, int pc, const float2* tw, bool inverse, cudaStream_t s) {
   constexpr int kZThreads = z_threads<LOGN>();
-  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / 16, LPC = kZThreads / TPL;
-  constexpr int LS = M + M / 16 + 2;
+  constexpr int N = 1 << LOGN, M = N / 2, TPL = M / z_values<LOGN>(), LPC = kZThreads / TPL;
+  constexpr int LS = z_line<LOGN>();
   const size_t smem = sizeof(float2) * (size_t)LS * LPC;
   unsigned grid = (unsigned)((nrows + LPC - 1) / LPC);
   if (inverse) {

@@ -416,6 +416,45 @@ def test_fft_2048_plane_wave_closed_form(pm):
         assert err < 1e-5 * N ** 3, (x, err)
 
 
+@pytest.mark.parametrize("N", [512, 1024, 2048])
+def test_fft_random_rows_match_numpy(pm, N):
+    """Random data on three z rows (i_r, j_r) of an otherwise empty N^3 mesh, N up to the
+    2048-point rows of the scale run: the r2c transform is, by linearity and the shift
+    theorem, sum_r e^{-2 pi i (k_x i_r + k_y j_r) / N} rfft(row_r)(k_z) -- every k_z mode of
+    each row's real transform, checked on whole (k_x, k_y) lines and sampled modes -- and
+    c2r of it is N^3 times the input (the rows, and zero elsewhere on sampled planes)."""
+    cfg = make_cfg(pm, nmesh=N, nc=0, nsites=0, n_max=16)
+    ctx = pm.ParticleMesh(cfg)
+    rows = ((0, 0), (5, N - 3), (N // 2 + 1, 17))
+    data = inputs.normal_values((len(rows), N), seed=N + 7).astype(np.float32)
+    mesh = torch.zeros((N, N, N), dtype=torch.float32, device="cuda")
+    for (i, j), r in zip(rows, data):
+        mesh[i, j] = torch.from_numpy(r).cuda()
+    out = ctx.fft_r2c(mesh)
+    ctx.sync()
+    R = np.fft.rfft(data.astype(np.float64), axis=1)          # (rows, N/2 + 1)
+    scale = np.abs(R).max() * len(rows)
+
+    def expected(kx, ky):
+        ph = np.array([np.exp(-2j * np.pi * (kx * i + ky * j) / N) for i, j in rows])
+        return (ph[:, None] * R).sum(axis=0)
+
+    rng = np.random.default_rng(N)
+    lines = [(0, 0), (1, 0), (0, N - 1), (N // 2, N // 2), (N - 1, 3)]
+    lines += [(int(rng.integers(0, N)), int(rng.integers(0, N))) for _ in range(20)]
+    for kx, ky in lines:
+        got = out[kx, ky].double().cpu().numpy()
+        err = np.abs(got[:, 0] + 1j * got[:, 1] - expected(kx, ky)).max() / scale
+        assert err < 3e-6, (kx, ky, err)
+    back = ctx.fft_c2r(out)
+    ctx.sync()
+    for (i, j), r in zip(rows, data):
+        err = np.abs(back[i, j].double().cpu().numpy() / N ** 3 - r).max() / np.abs(data).max()
+        assert err < 5e-6, (i, j, err)
+    for x in (1, N // 3, N - 1):
+        assert back[x].abs().max().item() < 5e-6 * N ** 3 * np.abs(data).max()
+
+
 def test_force_2048_stencil_matches_kspace_path(pm):
     """At 2048^3 there is no oracle: the default force (potential x pass on the TMA kernel,
     stencil readout) against the k-space per-component path (classic kernels, three
