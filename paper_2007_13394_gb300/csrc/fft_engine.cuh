@@ -286,6 +286,9 @@ __device__ __forceinline__ float2 gload(const float2* p) {
 // 2048 points: one exchange through shared memory fewer); ls is the row's shared-memory
 // line (z_line<LOGN, V>() float2).  Writes the N/2 + 1 modes k = 0 .. M over the row in
 // place.  ok = false: the thread takes part in the barriers only.
+// The split of the half-length transform Z into the real transform needs Z_k and
+// conj(Z_{M-k}): Z_k is the thread's own value, so only the mirrored one goes through
+// shared memory, unpadded (a lane-contiguous descending read, free of bank conflicts).
 template <int LOGN, bool WARP, bool CG, int V = 16>
 __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
@@ -295,43 +298,47 @@ __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int 
   for (int s = 0; s < V; ++s) v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
   run_stages<M, N, 1, false, V, WARP>(v, j, ls, 1, tw);
 #pragma unroll
-  for (int s = 0; s < V; ++s) ls[padv<V>(j + s * TPL)] = v[s];
+  for (int s = 0; s < V; ++s) ls[j + s * TPL] = v[s];
   line_sync<WARP>();
   if (ok) {
-    for (int k = j; k <= M; k += TPL) {
-      float2 zk = ls[padv<V>(k & (M - 1))];
-      float2 zm = cconj(ls[padv<V>((M - k) & (M - 1))]);
-      float2 e = cscale(cadd(zk, zm), 0.5f);
-      float2 o = cscale(csub(zk, zm), 0.5f);
-      float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
-      float2 wo = cmul(w, o);
+    auto mode = [&](int k, float2 zk, float2 zm) {
+      const float2 e = cscale(cadd(zk, zm), 0.5f);
+      const float2 o = cscale(csub(zk, zm), 0.5f);
+      const float2 w = __ldg(tw + k);           // e^{-2 pi i k / N}
+      const float2 wo = cmul(w, o);
       rp[k] = make_float2(e.x + wo.y, e.y - wo.x);  // e - i w o
+    };
+#pragma unroll
+    for (int s = 0; s < V; ++s) {
+      const int k = j + s * TPL;
+      mode(k, v[s], cconj(ls[(M - k) & (M - 1)]));
     }
+    if (j == 0) mode(M, v[0], cconj(v[0]));  // k = M: Z_0 and its own mirror
   }
 }
 
 // z pass, complex -> real, of one row in place (the inverse of z_r2c_row, unnormalised).
+// X_k is the thread's own loaded value; only conj(X_{M-k}) is read back from shared memory.
 template <int LOGN, bool WARP, bool CG, int V = 16>
 __device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / V;
-#pragma unroll
-  for (int s = 0; s < V; ++s) {
-    const int k = j + s * TPL;
-    ls[padv<V>(k)] = ok ? gload<CG>(rp + k) : make_float2(0.f, 0.f);
-  }
-  if (j == 0) ls[padv<V>(M)] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
-  line_sync<WARP>();
   float2 v[V];
 #pragma unroll
   for (int s = 0; s < V; ++s) {
+    v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
+    ls[j + s * TPL] = v[s];
+  }
+  if (j == 0) ls[M] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
+  line_sync<WARP>();
+#pragma unroll
+  for (int s = 0; s < V; ++s) {
     const int k = j + s * TPL;
-    float2 xk = ls[padv<V>(k)];
-    float2 xm = cconj(ls[padv<V>(M - k)]);
-    float2 e = cadd(xk, xm);
-    float2 d = csub(xk, xm);
-    float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
-    float2 wd = cmul(w, d);
+    const float2 xm = cconj(ls[M - k]);
+    const float2 e = cadd(v[s], xm);
+    const float2 d = csub(v[s], xm);
+    const float2 w = cconj(__ldg(tw + k));   // e^{+2 pi i k / N}
+    const float2 wd = cmul(w, d);
     v[s] = make_float2(e.x - wd.y, e.y + wd.x);  // e + i w d
   }
   line_sync<WARP>();
