@@ -354,9 +354,18 @@ template <int LOGN>
 __host__ __device__ constexpr int z_values() {
   return LOGN >= 10 ? 32 : 16;
 }
+// A row's M + M/V-pad + 2 float2, rounded up so that rows sharing a 16-lane phase of a
+// warp's 8-byte accesses (rows held by TPL < 16 threads) start TPL float2 apart modulo 16
+// and so fall into disjoint banks.
 template <int LOGN, int V = z_values<LOGN>()>
 __host__ __device__ constexpr int z_line() {
-  return (1 << (LOGN - 1)) + (1 << (LOGN - 1)) / (V >= 32 ? 32 : 16) + 2;
+  constexpr int M = 1 << (LOGN - 1), TPL = M / V;
+  constexpr int base = M + M / (V >= 32 ? 32 : 16) + 2;
+  if constexpr (TPL >= 16) {
+    return base;
+  } else {
+    return base + ((TPL - base % 16) % 16 + 16) % 16;
+  }
 }
 
 // Fused epilogue / prologue of the x pass.
