@@ -158,9 +158,9 @@ def source_digest(files=None):
 NCU_TRAFFIC = {
     # cfg3: the y passes (forward 34.43 + 34.88 GB, inverse 34.43 + 34.37 GB: their mean per
     # launch, as the kind's launches alternate) and the x pass of the potential
-    ("fft_y", "cfg3"): (lambda k: 69.06e9, "c40f3603e69f", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
+    ("fft_y", "cfg3"): (lambda k: 69.06e9, "b66013e27ead", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
                         "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2048^3 y passes, cfg3 step"),
-    ("fft_x_potential", "cfg3"): (lambda k: 68.96e9, "c40f3603e69f", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
+    ("fft_x_potential", "cfg3"): (lambda k: 68.96e9, "b66013e27ead", ("k_fft.cu", "fft_engine.cuh", "pm_internal.cuh"),
                                   "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 2048^3 x pass, cfg3 step"),
 }
 

@@ -270,17 +270,6 @@ __device__ __forceinline__ void run_stages_reg(float2 (&v)[V], int j, float2* sm
   if constexpr (!LAST) run_stages_reg<M, NS * R, INV, OFF + (NS > 1 ? (V / R) * (R - 1) : 0), NTW, V>(v, j, sm, cs, w);
 }
 
-// Global loads of the FFT passes: the default path, or ld.global.cg (L2 only), which the
-// fused (z, y) passes need because they read lines that other SMs wrote during the launch.
-template <bool CG>
-__device__ __forceinline__ float2 gload(const float2* p) {
-  if constexpr (CG) {
-    return __ldcg(p);
-  } else {
-    return *p;
-  }
-}
-
 // z pass, real -> complex, of one row: N reals read as M = N/2 complex values, held by
 // M/V threads (j = 0 .. M/V - 1) with V values each (V = 16, or 32 for rows of 1024 and
 // 2048 points: one exchange through shared memory fewer); ls is the row's shared-memory
@@ -289,13 +278,13 @@ __device__ __forceinline__ float2 gload(const float2* p) {
 // The split of the half-length transform Z into the real transform needs Z_k and
 // conj(Z_{M-k}): Z_k is the thread's own value, so only the mirrored one goes through
 // shared memory, unpadded (a lane-contiguous descending read, free of bank conflicts).
-template <int LOGN, bool WARP, bool CG, int V = 16>
+template <int LOGN, bool WARP, int V = 16>
 __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / V;
   float2 v[V];
 #pragma unroll
-  for (int s = 0; s < V; ++s) v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
+  for (int s = 0; s < V; ++s) v[s] = ok ? rp[j + s * TPL] : make_float2(0.f, 0.f);
   run_stages<M, N, 1, false, V, WARP>(v, j, ls, 1, tw);
 #pragma unroll
   for (int s = 0; s < V; ++s) ls[j + s * TPL] = v[s];
@@ -319,17 +308,17 @@ __device__ __forceinline__ void z_r2c_row(float2* __restrict__ rp, bool ok, int 
 
 // z pass, complex -> real, of one row in place (the inverse of z_r2c_row, unnormalised).
 // X_k is the thread's own loaded value; only conj(X_{M-k}) is read back from shared memory.
-template <int LOGN, bool WARP, bool CG, int V = 16>
+template <int LOGN, bool WARP, int V = 16>
 __device__ __forceinline__ void z_c2r_row(float2* __restrict__ rp, bool ok, int j, float2* ls,
                                           const float2* __restrict__ tw) {
   constexpr int N = 1 << LOGN, M = N / 2, TPL = M / V;
   float2 v[V];
 #pragma unroll
   for (int s = 0; s < V; ++s) {
-    v[s] = ok ? gload<CG>(rp + j + s * TPL) : make_float2(0.f, 0.f);
+    v[s] = ok ? rp[j + s * TPL] : make_float2(0.f, 0.f);
     ls[j + s * TPL] = v[s];
   }
-  if (j == 0) ls[M] = ok ? gload<CG>(rp + M) : make_float2(0.f, 0.f);
+  if (j == 0) ls[M] = ok ? rp[M] : make_float2(0.f, 0.f);
   line_sync<WARP>();
 #pragma unroll
   for (int s = 0; s < V; ++s) {

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(NT, z_min_blocks<LOGN>()) k_fft_z_r2c(float2* 
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  z_r2c_row<LOGN, WARP, false, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
+  z_r2c_row<LOGN, WARP, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 // z pass, complex -> real, in place.
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(NT, z_min_blocks<LOGN>()) k_fft_z_c2r(float2* 
   extern __shared__ float2 sm[];
   const int line = threadIdx.x / TPL, j = threadIdx.x % TPL;
   const long long row = (long long)blockIdx.x * LPC + line;
-  z_c2r_row<LOGN, WARP, false, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
+  z_c2r_row<LOGN, WARP, V>(data + row * pc, row < nrows, j, sm + line * LS, tw);
 }
 
 
